@@ -1,0 +1,134 @@
+/*
+ * poisson.h -- C ABI of the GB300 (sm_103a) pressure-Poisson projection library.
+ *
+ * The library implements the pressure step of the fully explicit projection method of
+ * Sec. 2 (Eqs. 4 and 7): on a staggered channel grid that is periodic in x and z and
+ * wall-bounded and stretched in y, it solves the discrete Poisson equation of Eq. 8 by
+ * real FFTs in x and z (Eq. 9), one wall-normal tridiagonal system per (kx, kz) solved by
+ * the PDD algorithm of Sec. 2.2 (Eqs. 10-21, exact reduced system) or by Thomas, and the
+ * inverse FFTs (steps (1)-(8) of Sec. 3.1).  The divergence of Eq. 7 and the velocity
+ * correction of Eq. 4 are fused around the solve.
+ *
+ * Conventions (all fields C-ordered, x fastest, contiguous, 16-byte aligned device memory):
+ *   cell fields (rhs, p)  : [ny][nz][nx]
+ *   u, w (x- / z-faces)   : [ny][nz][nx]; u[j][k][i] on the face between cells i-1 and i
+ *   v (y-faces)           : [ny+1][nz][nx]; v[0] and v[ny] are the two walls
+ *   y_faces               : ny+1 strictly increasing wall-normal face coordinates
+ * The discrete operator is L_h = D G (finite-volume form): homogeneous Neumann at the walls.
+ * poisson_solve returns the p with L_h p = rhs - <rhs> (volume-weighted mean removed, the
+ * compatibility condition) and zero volume-weighted mean (the gauge).
+ *
+ * Ownership: every device buffer, including the workspace, belongs to the caller; the plan
+ * owns only host memory.  Calls are stream-ordered and asynchronous unless stated.
+ * Errors: invalid arguments are reported synchronously as a poisson_status; launch errors
+ * as PS_ECUDA; device-side conditions (non-finite input when checked) go to a status word
+ * in the workspace, read by poisson_device_status.  The library never aborts or traps.
+ */
+#ifndef POISSON_H
+#define POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct poisson_plan_s* poisson_plan_t;
+
+typedef enum {
+  PS_OK = 0,
+  PS_EINVAL = 1,          /* bad argument: null pointer, bad size, misaligned buffer     */
+  PS_EUNSUPPORTED = 2,    /* valid but unsupported: nx, nz not 2^a 3^b, pdd_parts !| ny  */
+  PS_ENOMEM = 3,          /* host allocation failed                                      */
+  PS_ECUDA = 4,           /* a CUDA call or kernel launch failed                         */
+  PS_ETIMEOUT = 5,        /* a bounded device-side wait gave up                          */
+  PS_ENONFINITE = 6,      /* non-finite input detected (POISSON_CHECK_FINITE)            */
+  PS_ENOWORKSPACE = 7     /* poisson_set_workspace has not been called                   */
+} poisson_status;
+
+typedef enum {
+  PP_FP64 = 0,            /* FP64 in, FP64 arithmetic, FP64 out                          */
+  PP_FP32 = 1,            /* FP32 in/out; FP32 FFTs and sweeps; (0,0) and the lowest     */
+                          /* |kx|,|kz| <= fp64_low_modes systems in FP64                 */
+  PP_FP32_REFINED = 2     /* FP64 in/out; PP_FP32 solves plus refine_steps corrections   */
+                          /* driven by an FP64-accurate residual                          */
+} poisson_precision;
+
+typedef enum {
+  PT_AUTO = 0,            /* PDD (exact reduced system) with an automatic partition      */
+  PT_THOMAS = 1,          /* one serial Thomas sweep per system (pdd_parts = 1)          */
+  PT_PDD_EXACT = 2        /* PDD with pdd_parts sub-blocks, exact reduced system Eq. 21  */
+} poisson_tridiag;
+
+#define POISSON_CHECK_FINITE 0x1u   /* flag: scan inputs, set PS_ENONFINITE on NaN/Inf */
+
+typedef struct {
+  int nx, ny, nz;           /* cells; nx even, nx/2 and nz of the form 2^a 3^b; ny >= 2 */
+  double lx, lz;            /* periodic lengths                                          */
+  const double* y_faces;    /* host pointer, ny+1 values; copied during poisson_plan_create */
+  int precision;            /* poisson_precision                                         */
+  int tridiag;              /* poisson_tridiag                                           */
+  int pdd_parts;            /* PDD sub-blocks per system (divides ny); 0 = automatic     */
+  int fp64_low_modes;       /* PP_FP32*: systems with kx <= L and |kz| <= L run in FP64  */
+  int refine_steps;         /* PP_FP32_REFINED: number of residual corrections (>= 1)    */
+  unsigned flags;           /* POISSON_CHECK_FINITE                                      */
+} poisson_desc;
+
+/* Build a plan (host only; no CUDA call).  Validates the descriptor, factors the FFT
+ * lengths, computes the FP64 grid metrics (Sec. 2: stretched y), the modified wavenumbers
+ * of Eq. 9 and the FFT twiddles.  *out receives an opaque handle owned by the library. */
+poisson_status poisson_plan_create(const poisson_desc* desc, poisson_plan_t* out);
+
+/* Bytes of device workspace the plan needs (spectral buffer, tables, status word). */
+poisson_status poisson_workspace_size(poisson_plan_t plan, size_t* bytes);
+
+/* Attach caller-owned device workspace (>= poisson_workspace_size bytes, 256-byte aligned)
+ * and upload the plan's tables with stream-ordered copies on `stream` (a cudaStream_t). */
+poisson_status poisson_set_workspace(poisson_plan_t plan, void* workspace, size_t bytes,
+                                     void* stream);
+
+/* Solve L_h p = rhs - <rhs> with zero volume-weighted mean of p (Eqs. 7-9).
+ * rhs, p: device [ny][nz][nx]; FP64 for PP_FP64 and PP_FP32_REFINED, FP32 for PP_FP32.
+ * rhs == p (in place) is allowed. */
+poisson_status poisson_solve(poisson_plan_t plan, const void* rhs, void* p, void* stream);
+
+/* One projection (Eqs. 4 and 7): p solves L_h p = D(u_star) / dt (made compatible), then
+ * u = u_star - dt G p in place on u, v, w.  The wall faces of v are boundary values: they enter D
+ * and are not modified.  p_out (device [ny][nz][nx], may be NULL) receives p.
+ * Field dtype as for poisson_solve (PP_FP32_REFINED is not accepted here). */
+poisson_status projection_step(poisson_plan_t plan, void* u, void* v, void* w, void* p_out,
+                               double dt, void* stream);
+
+/* Adjoint of the velocity map of projection_step (which does not depend on dt):
+ * g <- g - D^T S^T G^T g in place, S the gauged solve.  Uses the same FFT and PDD kernels:
+ * L_h^T = W L_h W^-1 with W = diag(dy_j), so the transposed solve is a forward solve of a
+ * row-scaled right-hand side. */
+poisson_status projection_step_adjoint(poisson_plan_t plan, void* gu, void* gv, void* gw,
+                                       void* stream);
+
+/* End-to-end variant of projection_step on HOST buffers: copies u, v, w to the device
+ * staging buffers (caller-owned device memory of the field sizes), runs projection_step,
+ * copies u, v, w (and p when p_host != NULL, using p_dev) back and synchronises `stream`.
+ * Host buffers should be page-locked for asynchronous copies. */
+poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_host,
+                                    void* w_host, void* p_host, void* u_dev, void* v_dev,
+                                    void* w_dev, void* p_dev, double dt, void* stream);
+
+/* Synchronise `stream` and read the device status word (PS_OK, PS_ENONFINITE, ...),
+ * then clear it. */
+poisson_status poisson_device_status(poisson_plan_t plan, void* stream);
+
+/* Number of kernel launches the last call on this plan issued (for accounting). */
+int poisson_last_launch_count(poisson_plan_t plan);
+
+/* Free the host plan (does not touch the caller's workspace). NULL is accepted. */
+poisson_status poisson_plan_destroy(poisson_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* poisson_status_string(poisson_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POISSON_H */

@@ -68,10 +68,12 @@ def _spectral_solve(g: Grid, F, transposed: bool):
         lo, up = a, c
     lam = g.lambda_z()[:, None] + g.lambda_x()[None, :]          # (Nz, Nx)
     P = np.empty_like(F)
+    # the (0, 0) system is singular; its Thomas result is discarded and replaced below
     for k0 in range(0, g.nz, _CHUNK):
         k1 = min(g.nz, k0 + _CHUNK)
         diag = -(a + c)[:, None, None] + lam[None, k0:k1, :]
-        P[:, k0:k1, :] = thomas(lo[:, None, None], diag, up[:, None, None], F[:, k0:k1, :])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            P[:, k0:k1, :] = thomas(lo[:, None, None], diag, up[:, None, None], F[:, k0:k1, :])
     P[:, 0, 0] = _bordered_mode00(g, F[:, 0, 0], transposed)
     return P
 

@@ -1,0 +1,146 @@
+"""GB300 (sm_103a) pressure-Poisson projection for the staggered channel of Sec. 2.
+
+Python face of ``libpoisson.so``: ``Plan`` owns a plan and its torch-allocated workspace;
+``Plan.solve``, ``Plan.project`` and ``Plan.project_adjoint`` call the C ABI on the current
+torch stream; ``ProjectionFn`` wraps the projection and its hand-written adjoint in
+``torch.autograd.Function``.  All arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_PDD_EXACT,
+                      POISSON_CHECK_FINITE, PoissonError, check)
+
+__all__ = ["Plan", "ProjectionFn", "PoissonError", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
+           "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "POISSON_CHECK_FINITE"]
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Plan:
+    """A planned solve on one grid: nx x ny x nz cells, periodic lx, lz, wall-normal faces."""
+
+    def __init__(self, nx: int, ny: int, nz: int, y_faces, lx: float = 2 * np.pi, lz: float = np.pi,
+                 precision: int = PP_FP64, tridiag: int = PT_AUTO, pdd_parts: int = 0,
+                 fp64_low_modes: int = 4, refine_steps: int = 1, flags: int = 0, device=None):
+        L = _native.lib()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.precision = int(precision)
+        self.device = torch.device(device if device is not None else "cuda")
+        self._faces = np.ascontiguousarray(np.asarray(y_faces, dtype=np.float64))
+        if self._faces.size != self.ny + 1:
+            raise ValueError("y_faces must have ny + 1 entries")
+        desc = _native.PoissonDesc(self.nx, self.ny, self.nz, float(lx), float(lz),
+                                   self._faces.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   self.precision, int(tridiag), int(pdd_parts), int(fp64_low_modes),
+                                   int(refine_steps), int(flags))
+        h = ctypes.c_void_p()
+        check(L.poisson_plan_create(ctypes.byref(desc), ctypes.byref(h)), "poisson_plan_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        check(L.poisson_workspace_size(h, ctypes.byref(nbytes)), "poisson_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-self._ws.data_ptr()) % 256
+            check(L.poisson_set_workspace(h, self._ws.data_ptr() + off, self.workspace_bytes, _stream()),
+                  "poisson_set_workspace")
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.precision == PP_FP32 else torch.float64
+
+    @property
+    def cell_shape(self):
+        return (self.ny, self.nz, self.nx)
+
+    @property
+    def v_shape(self):
+        return (self.ny + 1, self.nz, self.nx)
+
+    def _check(self, t: torch.Tensor, shape, name: str):
+        if t.dtype != self.dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name}: expected contiguous CUDA {self.dtype} {tuple(shape)}, got "
+                             f"{t.dtype} {tuple(t.shape)} contiguous={t.is_contiguous()} device={t.device}")
+
+    def solve(self, rhs: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        self._check(rhs, self.cell_shape, "rhs")
+        if out is None:
+            out = torch.empty_like(rhs)
+        self._check(out, self.cell_shape, "out")
+        check(_native.lib().poisson_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "poisson_solve")
+        return out
+
+    def project(self, u, v, w, dt: float, p_out=None, stream=None):
+        """In-place projection of (u, v, w); returns p_out (or None)."""
+        self._check(u, self.cell_shape, "u")
+        self._check(v, self.v_shape, "v")
+        self._check(w, self.cell_shape, "w")
+        pp = 0
+        if p_out is not None:
+            self._check(p_out, self.cell_shape, "p_out")
+            pp = _ptr(p_out)
+        check(_native.lib().projection_step(self._h, _ptr(u), _ptr(v), _ptr(w), pp, float(dt), _stream(stream)),
+              "projection_step")
+        return p_out
+
+    def project_adjoint(self, gu, gv, gw, stream=None):
+        """In place: g <- P^T g (the adjoint of the projection's velocity map)."""
+        self._check(gu, self.cell_shape, "gu")
+        self._check(gv, self.v_shape, "gv")
+        self._check(gw, self.cell_shape, "gw")
+        check(_native.lib().projection_step_adjoint(self._h, _ptr(gu), _ptr(gv), _ptr(gw), _stream(stream)),
+              "projection_step_adjoint")
+
+    def project_host(self, u_h, v_h, w_h, dt: float, staging, p_h=None, stream=None):
+        """End-to-end projection of HOST (pinned) tensors through the library's host entry point."""
+        u_d, v_d, w_d, p_d = staging
+        check(_native.lib().projection_step_host(
+            self._h, _ptr(u_h), _ptr(v_h), _ptr(w_h), _ptr(p_h) if p_h is not None else 0,
+            _ptr(u_d), _ptr(v_d), _ptr(w_d), _ptr(p_d) if p_d is not None else 0, float(dt), _stream(stream)),
+            "projection_step_host")
+
+    def device_status(self, stream=None) -> int:
+        return int(_native.lib().poisson_device_status(self._h, _stream(stream)))
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(_native.lib().poisson_last_launch_count(self._h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _native._LIB is not None:
+            _native._LIB.poisson_plan_destroy(h)
+            self._h = None
+
+
+class ProjectionFn(torch.autograd.Function):
+    """u = P(u*) (Eqs. 4, 7) with the hand-written adjoint backward P^T (same FFT/PDD kernels)."""
+
+    @staticmethod
+    def forward(ctx, u, v, w, plan: Plan, dt: float):
+        ctx.plan = plan
+        uo, vo, wo = u.detach().clone(), v.detach().clone(), w.detach().clone()
+        plan.project(uo, vo, wo, dt)
+        return uo, vo, wo
+
+    @staticmethod
+    def backward(ctx, gu, gv, gw):
+        plan = ctx.plan
+        gu = gu.detach().clone().contiguous()
+        gv = gv.detach().clone().contiguous()
+        gw = gw.detach().clone().contiguous()
+        plan.project_adjoint(gu, gv, gw)
+        return gu, gv, gw, None, None

@@ -1,0 +1,84 @@
+"""ctypes binding of ``libpoisson.so`` (include/poisson.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only converts torch
+tensors to device pointers and the current torch stream to a ``cudaStream_t``.  There is no
+fallback: if the library is missing the import of ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpoisson.so")
+
+PS_OK, PS_EINVAL, PS_EUNSUPPORTED, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ENOWORKSPACE = range(8)
+PP_FP64, PP_FP32, PP_FP32_REFINED = 0, 1, 2
+PT_AUTO, PT_THOMAS, PT_PDD_EXACT = 0, 1, 2
+POISSON_CHECK_FINITE = 0x1
+
+# Every symbol declared in include/poisson.h.
+EXPORTS = (
+    "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
+    "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
+    "poisson_last_launch_count", "poisson_plan_destroy", "poisson_status_string",
+)
+
+
+class PoissonDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("lz", ctypes.c_double),
+        ("y_faces", ctypes.POINTER(ctypes.c_double)),
+        ("precision", ctypes.c_int), ("tridiag", ctypes.c_int), ("pdd_parts", ctypes.c_int),
+        ("fp64_low_modes", ctypes.c_int), ("refine_steps", ctypes.c_int), ("flags", ctypes.c_uint),
+    ]
+
+
+class PoissonError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpoisson.so (built in-tree by ``paper_2104_08863_gb300.build``); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L.poisson_plan_create.argtypes = [ctypes.POINTER(PoissonDesc), ctypes.POINTER(vp)]
+    L.poisson_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.poisson_set_workspace.argtypes = [vp, vp, sz, vp]
+    L.poisson_solve.argtypes = [vp, vp, vp, vp]
+    L.projection_step.argtypes = [vp, vp, vp, vp, vp, d, vp]
+    L.projection_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
+    L.projection_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, vp]
+    L.poisson_device_status.argtypes = [vp, vp]
+    L.poisson_last_launch_count.argtypes = [vp]
+    L.poisson_last_launch_count.restype = i
+    L.poisson_plan_destroy.argtypes = [vp]
+    L.poisson_status_string.argtypes = [i]
+    L.poisson_status_string.restype = ctypes.c_char_p
+    for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
+                 "projection_step", "projection_step_adjoint", "projection_step_host",
+                 "poisson_device_status", "poisson_plan_destroy"):
+        getattr(L, name).restype = i
+    _LIB = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().poisson_status_string(int(code)).decode()
+
+
+def check(code: int, where: str) -> None:
+    if code != PS_OK:
+        raise PoissonError(code, where)

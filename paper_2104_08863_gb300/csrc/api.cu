@@ -1,0 +1,459 @@
+// Host planner and C ABI of the pressure-Poisson library (include/poisson.h).
+//
+// poisson_plan_create validates the descriptor and computes, in FP64 on the host: the
+// stretched-grid metrics (Sec. 2; cell heights dy_j, centre distances h_j, the wall-normal
+// coefficients a_j = 1/(dy_j h_j), c_j = 1/(dy_j h_{j+1})), the modified wavenumbers of
+// Eq. 9 (lambda = -(4/d^2) sin^2(pi k / N)), the FFT factorisations and twiddles.  The solve
+// entry points run the pipeline of Sec. 3.1 steps (1)-(8) as a sequence of kernels on the
+// caller's stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace pp;
+
+struct poisson_plan_s {
+  Geometry g;
+  double lx, lz;
+  int precision, tridiag, parts, low, refine;
+  unsigned flags;
+  FftFactors fm, fz;
+  std::vector<double> faces, dy, h, a, c, lamx, lamz;
+  std::vector<unsigned char> host_tables;   // staging image of the device tables
+  // workspace layout (byte offsets)
+  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, ws_bytes;
+  size_t tab_offsets[32];
+  unsigned char* ws;
+  DevTables dt;
+  int launches;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool factor(int L, FftFactors& f) {
+  f.L = L;
+  f.nst = 0;
+  int r = L;
+  while (r % 8 == 0 && r > 4) { f.rad[f.nst++] = 8; r /= 8; }
+  while (r % 4 == 0) { f.rad[f.nst++] = 4; r /= 4; }
+  while (r % 2 == 0) { f.rad[f.nst++] = 2; r /= 2; }
+  while (r % 3 == 0) { f.rad[f.nst++] = 3; r /= 3; }
+  if (f.nst > 12) return false;
+  if (r != 1) return false;
+  if (f.nst == 0) { f.rad[f.nst++] = 1; }  // L == 1 is rejected by validation
+  return true;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int auto_parts(int ny) {
+  int best = 1;
+  for (int P = 2; P <= 32; ++P)
+    if (ny % P == 0 && ny / P >= 48) best = P;
+  return best;
+}
+
+template <typename T>
+void put_cplx_table(std::vector<unsigned char>& img, size_t off, const std::vector<double>& re,
+                    const std::vector<double>& im) {
+  T* p = reinterpret_cast<T*>(img.data() + off);
+  for (size_t i = 0; i < re.size(); ++i) { p[2 * i] = (T)re[i]; p[2 * i + 1] = (T)im[i]; }
+}
+template <typename T>
+void put_real_table(std::vector<unsigned char>& img, size_t off, const std::vector<double>& v) {
+  T* p = reinterpret_cast<T*>(img.data() + off);
+  for (size_t i = 0; i < v.size(); ++i) p[i] = (T)v[i];
+}
+
+bool spec_is_fp64(const poisson_plan_s* pl) { return pl->precision == PP_FP64; }
+
+}  // namespace
+
+extern "C" {
+
+const char* poisson_status_string(poisson_status s) {
+  switch (s) {
+    case PS_OK: return "ok";
+    case PS_EINVAL: return "invalid argument";
+    case PS_EUNSUPPORTED: return "unsupported size or option";
+    case PS_ENOMEM: return "host allocation failed";
+    case PS_ECUDA: return "CUDA error";
+    case PS_ETIMEOUT: return "device wait timed out";
+    case PS_ENONFINITE: return "non-finite input";
+    case PS_ENOWORKSPACE: return "workspace not set";
+  }
+  return "unknown status";
+}
+
+poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
+  if (!d || !out) return PS_EINVAL;
+  *out = nullptr;
+  if (d->nx < 4 || d->ny < 2 || d->nz < 2 || (d->nx & 1)) return PS_EINVAL;
+  if (!(d->lx > 0.0) || !(d->lz > 0.0) || !d->y_faces) return PS_EINVAL;
+  if (d->precision < PP_FP64 || d->precision > PP_FP32_REFINED) return PS_EINVAL;
+  if (d->tridiag < PT_AUTO || d->tridiag > PT_PDD_EXACT) return PS_EINVAL;
+  if ((long long)d->nx * d->ny * d->nz > (1LL << 34)) return PS_EUNSUPPORTED;
+  if (d->ny > 8192) return PS_EUNSUPPORTED;
+  for (int j = 0; j <= d->ny; ++j)
+    if (!isfinite(d->y_faces[j]) || (j > 0 && !(d->y_faces[j] > d->y_faces[j - 1]))) return PS_EINVAL;
+  poisson_plan_s* pl = new (std::nothrow) poisson_plan_s();
+  if (!pl) return PS_ENOMEM;
+  Geometry& g = pl->g;
+  g.nx = d->nx; g.ny = d->ny; g.nz = d->nz;
+  g.M = d->nx / 2;
+  g.ncols = g.M + 1;
+  const int cpad = d->precision == PP_FP64 ? 4 : 8;   // 64-byte aligned spectral rows
+  g.pitch = (g.ncols + cpad - 1) / cpad * cpad;
+  g.dx = d->lx / d->nx;
+  g.dz = d->lz / d->nz;
+  pl->lx = d->lx; pl->lz = d->lz;
+  pl->precision = d->precision;
+  pl->tridiag = d->tridiag;
+  pl->flags = d->flags;
+  if (!factor(g.M, pl->fm) || !factor(g.nz, pl->fz) || g.M < 2) { delete pl; return PS_EUNSUPPORTED; }
+  int P = 1;
+  if (d->tridiag == PT_THOMAS) P = 1;
+  else if (d->pdd_parts > 0) P = d->pdd_parts;
+  else P = auto_parts(g.ny);
+  if (P > 32 || g.ny % P != 0) { delete pl; return PS_EUNSUPPORTED; }
+  pl->parts = P;
+  int L = -1;
+  if (d->precision != PP_FP64) {
+    L = d->fp64_low_modes < 0 ? 0 : d->fp64_low_modes;
+    if (L > g.M) L = g.M;
+    if (2 * L + 1 > g.nz) L = (g.nz - 1) / 2;
+  }
+  pl->low = L;
+  pl->refine = d->precision == PP_FP32_REFINED ? (d->refine_steps > 0 ? d->refine_steps : 1) : 0;
+
+  // --- grid metrics (FP64) ---
+  const int ny = g.ny;
+  pl->faces.assign(d->y_faces, d->y_faces + ny + 1);
+  pl->dy.resize(ny);
+  std::vector<double> yc(ny);
+  for (int j = 0; j < ny; ++j) {
+    pl->dy[j] = pl->faces[j + 1] - pl->faces[j];
+    yc[j] = 0.5 * (pl->faces[j] + pl->faces[j + 1]);
+  }
+  pl->h.assign(ny + 1, 0.0);
+  for (int j = 1; j < ny; ++j) pl->h[j] = yc[j] - yc[j - 1];
+  pl->a.assign(ny, 0.0);
+  pl->c.assign(ny, 0.0);
+  for (int j = 1; j < ny; ++j) pl->a[j] = 1.0 / (pl->dy[j] * pl->h[j]);
+  for (int j = 0; j < ny - 1; ++j) pl->c[j] = 1.0 / (pl->dy[j] * pl->h[j + 1]);
+  pl->lamx.resize(g.ncols);
+  for (int k = 0; k < g.ncols; ++k) {
+    const double s = sin(M_PI * k / g.nx);
+    pl->lamx[k] = -(4.0 / (g.dx * g.dx)) * s * s;
+  }
+  pl->lamz.resize(g.nz);
+  for (int k = 0; k < g.nz; ++k) {
+    const double s = sin(M_PI * k / g.nz);
+    pl->lamz[k] = -(4.0 / (g.dz * g.dz)) * s * s;
+  }
+  // --- twiddles (FP64 trig, index-reduced angles) ---
+  auto twid = [](int L, int n, std::vector<double>& re, std::vector<double>& im) {
+    re.resize(n); im.resize(n);
+    for (int t = 0; t < n; ++t) {
+      const double ang = -2.0 * M_PI * (double)t / (double)L;
+      re[t] = cos(ang); im[t] = sin(ang);
+    }
+  };
+  std::vector<double> twm_r, twm_i, twp_r, twp_i, twz_r, twz_i;
+  twid(g.M, g.M, twm_r, twm_i);
+  twid(g.nx, g.M + 1, twp_r, twp_i);
+  twid(g.nz, g.nz, twz_r, twz_i);
+
+  // --- table image: double tables then float tables ---
+  size_t off = 0;
+  size_t* to = pl->tab_offsets;
+  auto slot = [&](int id, size_t bytes) { to[id] = off; off = align_up(off + bytes, 256); };
+  slot(0, 16 * (size_t)g.M);  slot(1, 16 * (size_t)(g.M + 1)); slot(2, 16 * (size_t)g.nz);
+  slot(3, 8 * (size_t)ny);    slot(4, 8 * (size_t)ny);
+  slot(5, 8 * (size_t)g.M);   slot(6, 8 * (size_t)(g.M + 1)); slot(7, 8 * (size_t)g.nz);
+  slot(8, 4 * (size_t)ny);    slot(9, 4 * (size_t)ny);
+  slot(10, 8 * (size_t)g.ncols); slot(11, 8 * (size_t)g.nz);
+  slot(12, 8 * (size_t)ny);   slot(13, 8 * (size_t)(ny + 1));
+  const size_t tab_bytes = off;
+  pl->host_tables.assign(tab_bytes, 0);
+  auto& img = pl->host_tables;
+  put_cplx_table<double>(img, to[0], twm_r, twm_i);
+  put_cplx_table<double>(img, to[1], twp_r, twp_i);
+  put_cplx_table<double>(img, to[2], twz_r, twz_i);
+  put_real_table<double>(img, to[3], pl->a);
+  put_real_table<double>(img, to[4], pl->c);
+  put_cplx_table<float>(img, to[5], twm_r, twm_i);
+  put_cplx_table<float>(img, to[6], twp_r, twp_i);
+  put_cplx_table<float>(img, to[7], twz_r, twz_i);
+  put_real_table<float>(img, to[8], pl->a);
+  put_real_table<float>(img, to[9], pl->c);
+  put_real_table<double>(img, to[10], pl->lamx);
+  put_real_table<double>(img, to[11], pl->lamz);
+  put_real_table<double>(img, to[12], pl->dy);
+  put_real_table<double>(img, to[13], pl->h);
+
+  // --- workspace layout ---
+  const size_t csz = spec_is_fp64(pl) ? 16 : 8;
+  const size_t rsz = spec_is_fp64(pl) ? 8 : 4;
+  off = 0;
+  pl->off_spec = off;  off = align_up(off + csz * (size_t)ny * g.nz * g.pitch, 256);
+  pl->off_pbuf = off;  off = align_up(off + rsz * (size_t)ny * g.nz * g.nx, 256);
+  pl->off_scratch = off;
+  if (L >= 0) off = align_up(off + 16 * (size_t)ny * (L + 1) * (2 * L + 1), 256);
+  pl->off_tables = off; off = align_up(off + tab_bytes, 256);
+  pl->off_status = off; off = align_up(off + 256, 256);
+  pl->ws_bytes = off;
+  pl->ws = nullptr;
+  pl->launches = 0;
+  *out = pl;
+  return PS_OK;
+}
+
+poisson_status poisson_workspace_size(poisson_plan_t pl, size_t* bytes) {
+  if (!pl || !bytes) return PS_EINVAL;
+  *bytes = pl->ws_bytes;
+  return PS_OK;
+}
+
+poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, void* stream) {
+  if (!pl || !ws) return PS_EINVAL;
+  if (bytes < pl->ws_bytes || ((uintptr_t)ws & 255u)) return PS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* base = (unsigned char*)ws;
+  cudaError_t e = cudaMemcpyAsync(base + pl->off_tables, pl->host_tables.data(), pl->host_tables.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return PS_ECUDA;
+  e = cudaMemsetAsync(base + pl->off_status, 0, 256, st);
+  if (e != cudaSuccess) return PS_ECUDA;
+  // The host image must outlive the copy; synchronise once here (set-up, not the hot path).
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return PS_ECUDA;
+  pl->ws = base;
+  unsigned char* tb = base + pl->off_tables;
+  const size_t* to = pl->tab_offsets;
+  DevTables& dt = pl->dt;
+  dt.d.tw_m = (const cplx<double>*)(tb + to[0]);
+  dt.d.tw_post = (const cplx<double>*)(tb + to[1]);
+  dt.d.tw_z = (const cplx<double>*)(tb + to[2]);
+  dt.d.a = (const double*)(tb + to[3]);
+  dt.d.c = (const double*)(tb + to[4]);
+  dt.f.tw_m = (const cplx<float>*)(tb + to[5]);
+  dt.f.tw_post = (const cplx<float>*)(tb + to[6]);
+  dt.f.tw_z = (const cplx<float>*)(tb + to[7]);
+  dt.f.a = (const float*)(tb + to[8]);
+  dt.f.c = (const float*)(tb + to[9]);
+  dt.lamx = (const double*)(tb + to[10]);
+  dt.lamz = (const double*)(tb + to[11]);
+  dt.dy = (const double*)(tb + to[12]);
+  dt.h = (const double*)(tb + to[13]);
+  dt.status = (int*)(base + pl->off_status);
+  return PS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+#define PP_TRY(expr)                                   \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    ++pl->launches;                                    \
+    if (_e != cudaSuccess) return PS_ECUDA;            \
+  } while (0)
+
+// Spectral middle of a solve on the plan's spectral buffer: forward z-FFT, wall-normal
+// systems, (0, 0) mode, inverse z-FFT.
+template <typename T>
+poisson_status spectral_core(poisson_plan_s* pl, cplx<T>* spec, cudaStream_t st);
+
+template <>
+poisson_status spectral_core<double>(poisson_plan_s* pl, cplx<double>* spec, cudaStream_t st) {
+  const Geometry& g = pl->g;
+  PP_TRY(launch_fft_z<double>(g, pl->dt, pl->fz, -1, spec, st));
+  PP_TRY((launch_tridiag<double, double>(g, pl->dt, pl->parts, -1, false, spec, st)));
+  PP_TRY(launch_mode00<double>(g, pl->dt, false, spec, st));
+  PP_TRY(launch_fft_z<double>(g, pl->dt, pl->fz, +1, spec, st));
+  return PS_OK;
+}
+
+template <>
+poisson_status spectral_core<float>(poisson_plan_s* pl, cplx<float>* spec, cudaStream_t st) {
+  const Geometry& g = pl->g;
+  PP_TRY(launch_fft_z<float>(g, pl->dt, pl->fz, -1, spec, st));
+  PP_TRY((launch_tridiag<float, float>(g, pl->dt, pl->parts, pl->low, false, spec, st)));
+  if (pl->low >= 0) {
+    cplx<double>* scr = (cplx<double>*)(pl->ws + pl->off_scratch);
+    PP_TRY(launch_tridiag_low64(g, pl->dt, pl->parts, pl->low, spec, scr, st));
+  }
+  PP_TRY(launch_mode00<float>(g, pl->dt, false, spec, st));
+  PP_TRY(launch_fft_z<float>(g, pl->dt, pl->fz, +1, spec, st));
+  return PS_OK;
+}
+
+template <typename T, typename TI>
+poisson_status forward_and_core(poisson_plan_s* pl, FwdMode mode, const FwdArgs& args, cudaStream_t st) {
+  cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
+  PP_TRY((launch_fwd_x<T, TI>(pl->g, pl->dt, pl->fm, mode, args, spec, st)));
+  return spectral_core<T>(pl, spec, st);
+}
+
+template <typename T, typename TO>
+poisson_status inverse_x(poisson_plan_s* pl, InvMode mode, TO* out, cudaStream_t st) {
+  cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
+  const double scale = 1.0 / ((double)pl->g.nx * (double)pl->g.nz);
+  PP_TRY((launch_inv_x<T, TO>(pl->g, pl->dt, pl->fm, mode, spec, out, scale, st)));
+  return PS_OK;
+}
+
+size_t cell_count(const poisson_plan_s* pl) { return (size_t)pl->g.ny * pl->g.nz * pl->g.nx; }
+size_t vface_count(const poisson_plan_s* pl) { return (size_t)(pl->g.ny + 1) * pl->g.nz * pl->g.nx; }
+
+template <typename T>
+poisson_status check_finite(poisson_plan_s* pl, const void* x, size_t n, cudaStream_t st) {
+  if (!(pl->flags & POISSON_CHECK_FINITE)) return PS_OK;
+  PP_TRY(launch_check_finite<T>((const T*)x, n, pl->dt.status, st));
+  return PS_OK;
+}
+
+}  // namespace
+
+#define PP_RET(expr)                     \
+  do {                                   \
+    poisson_status _s = (expr);          \
+    if (_s != PS_OK) return _s;          \
+  } while (0)
+
+extern "C" {
+
+poisson_status poisson_solve(poisson_plan_t pl, const void* rhs, void* p, void* stream) {
+  if (!pl || !rhs || !p) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!aligned16(rhs) || !aligned16(p)) return PS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  pl->launches = 0;
+  FwdArgs args = {};
+  args.in = rhs;
+  args.in_scale = 1.0;
+  if (pl->precision == PP_FP64) {
+    PP_RET(check_finite<double>(pl, rhs, cell_count(pl), st));
+    PP_RET((forward_and_core<double, double>(pl, FWD_PLAIN, args, st)));
+    PP_RET((inverse_x<double, double>(pl, INV_STORE, (double*)p, st)));
+  } else if (pl->precision == PP_FP32) {
+    PP_RET(check_finite<float>(pl, rhs, cell_count(pl), st));
+    PP_RET((forward_and_core<float, float>(pl, FWD_PLAIN, args, st)));
+    PP_RET((inverse_x<float, float>(pl, INV_STORE, (float*)p, st)));
+  } else {
+    if (rhs == p) return PS_EINVAL;   // the residual re-reads rhs after p is written
+    PP_RET(check_finite<double>(pl, rhs, cell_count(pl), st));
+    PP_RET((forward_and_core<float, double>(pl, FWD_PLAIN, args, st)));
+    PP_RET((inverse_x<float, double>(pl, INV_STORE, (double*)p, st)));
+    for (int r = 0; r < pl->refine; ++r) {
+      FwdArgs ra = {};
+      ra.in = rhs;
+      ra.p = p;
+      ra.in_scale = 1.0;
+      PP_RET((forward_and_core<float, double>(pl, FWD_RESID, ra, st)));
+      PP_RET((inverse_x<float, double>(pl, INV_ACCUM, (double*)p, st)));
+    }
+  }
+  return PS_OK;
+}
+
+poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, void* p_out, double dt,
+                               void* stream) {
+  if (!pl || !u || !v || !w) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!(dt > 0.0) || !isfinite(dt)) return PS_EINVAL;
+  if (!aligned16(u) || !aligned16(v) || !aligned16(w) || (p_out && !aligned16(p_out))) return PS_EINVAL;
+  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  pl->launches = 0;
+  FwdArgs args = {};
+  args.u = u; args.v = v; args.w = w;
+  args.in_scale = 1.0 / dt;
+  if (pl->precision == PP_FP64) {
+    double* p = p_out ? (double*)p_out : (double*)(pl->ws + pl->off_pbuf);
+    PP_RET(check_finite<double>(pl, u, cell_count(pl), st));
+    PP_RET((forward_and_core<double, double>(pl, FWD_DIV, args, st)));
+    PP_RET((inverse_x<double, double>(pl, INV_STORE, p, st)));
+    PP_TRY(launch_gradient<double>(pl->g, pl->dt, p, (double*)u, (double*)v, (double*)w, dt, st));
+  } else {
+    float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
+    PP_RET(check_finite<float>(pl, u, cell_count(pl), st));
+    PP_RET((forward_and_core<float, float>(pl, FWD_DIV, args, st)));
+    PP_RET((inverse_x<float, float>(pl, INV_STORE, p, st)));
+    PP_TRY(launch_gradient<float>(pl->g, pl->dt, p, (float*)u, (float*)v, (float*)w, dt, st));
+  }
+  return PS_OK;
+}
+
+poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, void* gw, void* stream) {
+  if (!pl || !gu || !gv || !gw) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!aligned16(gu) || !aligned16(gv) || !aligned16(gw)) return PS_EINVAL;
+  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  pl->launches = 0;
+  FwdArgs args = {};
+  args.u = gu; args.v = gv; args.w = gw;
+  args.in_scale = 1.0;
+  if (pl->precision == PP_FP64) {
+    double* q = (double*)(pl->ws + pl->off_pbuf);
+    PP_RET((forward_and_core<double, double>(pl, FWD_GRADT, args, st)));
+    PP_RET((inverse_x<double, double>(pl, INV_STORE, q, st)));
+    PP_TRY(launch_adjoint_epilogue<double>(pl->g, pl->dt, q, (double*)gu, (double*)gv, (double*)gw, st));
+  } else {
+    float* q = (float*)(pl->ws + pl->off_pbuf);
+    PP_RET((forward_and_core<float, float>(pl, FWD_GRADT, args, st)));
+    PP_RET((inverse_x<float, float>(pl, INV_STORE, q, st)));
+    PP_TRY(launch_adjoint_epilogue<float>(pl->g, pl->dt, q, (float*)gu, (float*)gv, (float*)gw, st));
+  }
+  return PS_OK;
+}
+
+poisson_status projection_step_host(poisson_plan_t pl, void* u_h, void* v_h, void* w_h, void* p_h, void* u_d,
+                                    void* v_d, void* w_d, void* p_d, double dt, void* stream) {
+  if (!pl || !u_h || !v_h || !w_h || !u_d || !v_d || !w_d) return PS_EINVAL;
+  if (p_h && !p_d) return PS_EINVAL;
+  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = pl->precision == PP_FP64 ? 8 : 4;
+  const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
+  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  PP_RET(projection_step(pl, u_d, v_d, w_d, p_h ? p_d : nullptr, dt, stream));
+  if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (p_h && cudaMemcpyAsync(p_h, p_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  return PS_OK;
+}
+
+poisson_status poisson_device_status(poisson_plan_t pl, void* stream) {
+  if (!pl) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, pl->dt.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemsetAsync(pl->dt.status, 0, sizeof(int), st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  return (poisson_status)h;
+}
+
+int poisson_last_launch_count(poisson_plan_t pl) { return pl ? pl->launches : -1; }
+
+poisson_status poisson_plan_destroy(poisson_plan_t pl) {
+  delete pl;
+  return PS_OK;
+}
+
+}  // extern "C"

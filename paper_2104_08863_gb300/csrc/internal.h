@@ -1,0 +1,96 @@
+// Host-side plan and kernel launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <vector>
+
+#include "../../include/poisson.h"
+#include "fft.cuh"
+
+namespace pp {
+
+// Device-side table pointers for one arithmetic type T.
+template <typename T> struct Tables {
+  const cplx<T>* tw_m;     // e^{-2 pi i t / M}, t < M   (half-length complex FFT in x)
+  const cplx<T>* tw_post;  // e^{-2 pi i k / Nx}, k <= M (real-to-complex packing)
+  const cplx<T>* tw_z;     // e^{-2 pi i t / Nz}, t < Nz
+  const T* a;              // wall-normal sub-diagonal a_j  (0 for j = 0)
+  const T* c;              // wall-normal super-diagonal c_j (0 for j = ny-1)
+};
+
+struct DevTables {
+  Tables<double> d;
+  Tables<float> f;
+  const double* lamx;      // lambda_x(kx), kx = 0..M   (Eq. 9 eigenvalues)
+  const double* lamz;      // lambda_z(kz), kz = 0..nz-1
+  const double* dy;        // cell heights dy_j
+  const double* h;         // centre distances across face j (j = 1..ny-1; h[0], h[ny] = 0)
+  int* status;             // device status word
+};
+
+struct Geometry {
+  int nx, ny, nz, M, ncols, pitch;
+  double dx, dz;
+};
+
+struct LaunchCount {
+  int n = 0;
+};
+
+// --- launchers (return cudaGetLastError() after the launch) --------------------------
+enum FwdMode { FWD_PLAIN = 0, FWD_DIV = 1, FWD_RESID = 2, FWD_GRADT = 3 };
+enum InvMode { INV_STORE = 0, INV_ACCUM = 1, INV_ADJ = 2 };
+
+struct FwdArgs {
+  const void* in;        // FWD_PLAIN / FWD_RESID: rhs field
+  const void* u;         // FWD_DIV / FWD_GRADT: face fields
+  const void* v;
+  const void* w;
+  const void* p;         // FWD_RESID: current pressure (FP64)
+  double in_scale;       // FWD_DIV: 1/dt; FWD_PLAIN: 1
+};
+
+template <typename T, typename TI>
+cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, FwdMode mode,
+                         const FwdArgs& args, cplx<T>* spec, cudaStream_t st);
+
+template <typename T, typename TO>
+cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
+                         const cplx<T>* spec, TO* out, double scale, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
+                         cudaStream_t st);
+
+template <typename TD, typename TC>
+cudaError_t launch_tridiag(const Geometry& g, const DevTables& tb, int parts, int low_modes, bool low_list,
+                           cplx<TD>* spec, cudaStream_t st);
+
+template <>
+cudaError_t launch_tridiag<double, double>(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                           bool low_list, cplx<double>* spec, cudaStream_t st);
+template <>
+cudaError_t launch_tridiag<float, float>(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                         bool low_list, cplx<float>* spec, cudaStream_t st);
+
+// FP64 re-solve of the low-mode list on FP32 spectral data (intermediates in FP64 scratch).
+cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                 cplx<float>* spec, cplx<double>* scratch, cudaStream_t st);
+
+template <typename TD>
+cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, bool transposed_gauge, cplx<TD>* spec,
+                          cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
+                            cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, const T* q, T* gu, T* gv, T* gw,
+                                    cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st);
+
+}  // namespace pp

@@ -1,0 +1,117 @@
+// Pointwise stencil passes around the solve.
+//
+//  k_gradient  : the velocity correction of Eq. 4, u <- u - dt G p, on the staggered faces;
+//                wall faces of v are boundary values and are left unchanged (Sec. 2).
+//  k_adj_epi   : the adjoint epilogue g <- g - D^T q with q = W p' (W = diag(dy_j)), where p'
+//                solves L_h p' = W^-1 G^T g; this is P^T g = g - D^T S^T G^T g because
+//                L_h^T = W L_h W^-1 and the forward gauge (zero dy-weighted mean of p') is the
+//                zero-sum gauge of q.
+//  k_check_finite : sets the device status word when a value is NaN or Inf.
+#include "internal.h"
+
+namespace pp {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gradient(Geometry g, const T* __restrict__ p, T* __restrict__ u,
+                                                  T* __restrict__ v, T* __restrict__ w,
+                                                  const double* __restrict__ h, T dt) {
+  const size_t plane = (size_t)g.nz * g.nx;
+  const size_t total = (size_t)(g.ny + 1) * plane;
+  const T cx = dt / T(g.dx), cz = dt / T(g.dz);
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const size_t r = idx - (size_t)j * plane;
+    const int k = (int)(r / g.nx);
+    const int i = (int)(r - (size_t)k * g.nx);
+    if (j < g.ny) {
+      const T pc = p[idx];
+      const T pxm = p[idx - i + (i == 0 ? g.nx - 1 : i - 1)];
+      const T pzm = p[(size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i];
+      u[idx] -= cx * (pc - pxm);
+      w[idx] -= cz * (pc - pzm);
+    }
+    if (j >= 1 && j <= g.ny - 1) {
+      const T cy = dt / T(h[j]);
+      v[idx] -= cy * (p[idx] - p[idx - plane]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_epi(Geometry g, const T* __restrict__ pp_, T* __restrict__ gu,
+                                                 T* __restrict__ gv, T* __restrict__ gw,
+                                                 const double* __restrict__ dy) {
+  const size_t plane = (size_t)g.nz * g.nx;
+  const size_t total = (size_t)(g.ny + 1) * plane;
+  const T ix = T(1.0 / g.dx), iz = T(1.0 / g.dz);
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const size_t r = idx - (size_t)j * plane;
+    const int k = (int)(r / g.nx);
+    const int i = (int)(r - (size_t)k * g.nx);
+    if (j < g.ny) {
+      const T dyj = T(dy[j]);
+      const T pc = pp_[idx];
+      const T pxm = pp_[idx - i + (i == 0 ? g.nx - 1 : i - 1)];
+      const T pzm = pp_[(size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i];
+      gu[idx] -= dyj * (pxm - pc) * ix;
+      gw[idx] -= dyj * (pzm - pc) * iz;
+    }
+    // (D_y^T q)_f = q_{f-1}/dy_{f-1} - q_f/dy_f = p'_{f-1} - p'_f  (terms outside 0..ny-1 vanish)
+    T t = T(0);
+    if (j >= 1) t += pp_[idx - plane];
+    if (j <= g.ny - 1) t -= pp_[idx];
+    gv[idx] -= t;
+  }
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ x, size_t n, int* status) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(status, (int)DEV_NONFINITE);
+}
+
+static int stream_grid(size_t total) {
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = 152 * 16;
+  return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+template <typename T>
+cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
+                            cudaStream_t st) {
+  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
+  k_gradient<T><<<stream_grid(total), 256, 0, st>>>(g, p, u, v, w, tb.h, T(dt));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, const T* q, T* gu, T* gv, T* gw,
+                                    cudaStream_t st) {
+  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
+  k_adj_epi<T><<<stream_grid(total), 256, 0, st>>>(g, q, gu, gv, gw, tb.dy);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st) {
+  k_check_finite<T><<<stream_grid(n), 256, 0, st>>>(x, n, status);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gradient<double>(const Geometry&, const DevTables&, const double*, double*, double*,
+                                             double*, double, cudaStream_t);
+template cudaError_t launch_gradient<float>(const Geometry&, const DevTables&, const float*, float*, float*, float*,
+                                            double, cudaStream_t);
+template cudaError_t launch_adjoint_epilogue<double>(const Geometry&, const DevTables&, const double*, double*,
+                                                     double*, double*, cudaStream_t);
+template cudaError_t launch_adjoint_epilogue<float>(const Geometry&, const DevTables&, const float*, float*, float*,
+                                                    float*, cudaStream_t);
+template cudaError_t launch_check_finite<double>(const double*, size_t, int*, cudaStream_t);
+template cudaError_t launch_check_finite<float>(const float*, size_t, int*, cudaStream_t);
+
+}  // namespace pp

@@ -1,0 +1,93 @@
+"""Host-side tests of the C ABI: the library loads, exports what include/poisson.h declares,
+and validates descriptors without touching a GPU (poisson_plan_create makes no CUDA call)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2104_08863_gb300 import build as b
+    b.build()
+    from paper_2104_08863_gb300 import _native
+    return _native
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "poisson.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    names = _header_functions()
+    assert len(names) >= 10
+    lib = ctypes.CDLL(native.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(native.EXPORTS) == names
+
+
+def _desc(native, nx=32, ny=32, nz=32, faces=None, **kw):
+    faces = W.tanh_faces(ny, 1.5) if faces is None else faces
+    arr = np.ascontiguousarray(faces, dtype=np.float64)
+    d = native.PoissonDesc(nx, ny, nz, 2 * np.pi, np.pi, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           kw.get("precision", 0), kw.get("tridiag", 0), kw.get("pdd_parts", 0),
+                           kw.get("fp64_low_modes", 4), kw.get("refine_steps", 1), kw.get("flags", 0))
+    return d, arr
+
+
+def _create(native, d):
+    h = ctypes.c_void_p()
+    st = native.lib().poisson_plan_create(ctypes.byref(d), ctypes.byref(h))
+    if st == 0:
+        size = ctypes.c_size_t()
+        assert native.lib().poisson_workspace_size(h, ctypes.byref(size)) == 0
+        native.lib().poisson_plan_destroy(h)
+        return st, size.value
+    return st, None
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(nx=31), 1), (dict(nx=2), 1), (dict(nz=1), 1), (dict(ny=1, faces=np.array([-1.0, 1.0])), 1),
+    (dict(nx=28), 2), (dict(nz=14), 2), (dict(nx=20), 2),
+    (dict(tridiag=2, pdd_parts=5), 2), (dict(tridiag=2, pdd_parts=64, ny=64, faces=W.tanh_faces(64, 1.0)), 2),
+    (dict(precision=7), 1), (dict(tridiag=9), 1),
+])
+def test_plan_rejects_invalid_or_unsupported(native, kw, expect):
+    d, _ = _desc(native, **kw)
+    st, _ = _create(native, d)
+    assert st == expect
+
+
+def test_plan_rejects_non_monotone_faces(native):
+    f = W.tanh_faces(32, 1.5)
+    f[5], f[6] = f[6], f[5]
+    d, _ = _desc(native, faces=f)
+    assert _create(native, d)[0] == 1
+    f2 = W.tanh_faces(32, 1.5)
+    f2[3] = np.nan
+    d, _ = _desc(native, faces=f2)
+    assert _create(native, d)[0] == 1
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(32, 32, 32), (6, 8, 12), (96, 48, 27), (1536, 768, 1024)])
+def test_plan_accepts_radix_2_3_sizes_and_reports_workspace(native, nx, ny, nz):
+    d, _ = _desc(native, nx=nx, ny=ny, nz=nz, faces=W.tanh_faces(ny, 2.0))
+    st, size = _create(native, d)
+    assert st == 0
+    spectral = ny * nz * (nx // 2 + 1) * 16
+    assert size >= spectral
+
+
+def test_status_strings(native):
+    assert native.status_string(0) == "ok"
+    assert "invalid" in native.status_string(1)
+    assert native.status_string(99) == "unknown status"

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances (relative to the largest magnitude of the oracle result):
+* FP64 (PP_FP64): 1e-12.
+* FP32 (PP_FP32): 2e-5  -- FP32 FFTs (~1e-7 log2 N) and FP32 margin-Thomas (~1e-6 on the
+  weakest modes); the lowest modes run in FP64.
+* FP32 + refinement (PP_FP32_REFINED): one correction squares the FP32 error
+  (eps <= 2e-5 -> eps^2 ~ 4e-10, with an O(1) growth factor): 2e-9; two corrections reach the
+  FP64 residual's floor: 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_08863_gb300 import build as b
+    b.build()
+    import paper_2104_08863_gb300 as mod
+    return mod
+
+
+def relerr(got, want):
+    return float(np.max(np.abs(np.asarray(got) - want)) / np.max(np.abs(want)))
+
+
+def to_dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+def solve_gpu(P, plan, f, dtype=torch.float64):
+    ft = to_dev(f, dtype)
+    out = plan.solve(ft)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+# ------------------------------------------------------------------------------ FP64 solve
+
+@pytest.mark.parametrize("rhs", ["manufactured", "random_divergence"])
+@pytest.mark.parametrize("tridiag,parts", [(1, 1), (2, 4), (2, 8)])
+def test_fp64_solve_channel32(P, rhs, tridiag, parts):
+    case = W.CHANNEL_32
+    faces = W.tanh_faces(case.ny, case.stretch)
+    g = oracle.Grid(case.nx, case.nz, faces)
+    if rhs == "manufactured":
+        f = W.manufactured_rhs(case.nx, case.ny, case.nz, faces)
+    else:
+        f = oracle.divergence(g, *W.random_velocity(0, case.nx, case.ny, case.nz))
+    want = oracle.solve(g, f)
+    plan = P.Plan(case.nx, case.ny, case.nz, faces, precision=P.PP_FP64, tridiag=tridiag, pdd_parts=parts,
+                  device=DEV)
+    got = solve_gpu(P, plan, f)
+    assert relerr(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,nz,parts", [
+    (4, 2, 2, 1), (6, 6, 3, 3), (12, 10, 9, 5), (24, 12, 18, 4), (48, 16, 27, 16), (96, 24, 12, 6),
+    (64, 48, 96, 8), (192, 36, 8, 2), (384, 8, 6, 8), (128, 64, 256, 32), (8, 96, 1536, 3),
+])
+def test_fp64_solve_ragged_sizes(P, nx, ny, nz, parts):
+    faces = W.tanh_faces(ny, 1.7)
+    g = oracle.Grid(nx, nz, faces)
+    f = W.random_field(21, (ny, nz, nx))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, tridiag=P.PT_PDD_EXACT, pdd_parts=parts, device=DEV)
+    got = solve_gpu(P, plan, f)
+    assert relerr(got, want) <= 1e-12
+
+
+def test_fp64_solve_in_place_and_repeatable(P):
+    nx, ny, nz = 24, 16, 12
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    f = W.random_field(22, (ny, nz, nx))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, pdd_parts=2, device=DEV)
+    ft = to_dev(f)
+    plan.solve(ft, out=ft)
+    a = ft.cpu().numpy()
+    assert relerr(a, want) <= 1e-12
+    b = solve_gpu(P, plan, f)
+    assert np.array_equal(b, solve_gpu(P, plan, f))
+
+
+def test_fp64_closed_form_uniform_grid(P):
+    nx, ny, nz = 16, 12, 8
+    faces = W.uniform_faces(ny)
+    g = oracle.Grid(nx, nz, faces)
+    x = (np.arange(nx) + 0.5) * g.dx
+    z = (np.arange(nz) + 0.5) * g.dz
+    yc = -1.0 + (np.arange(ny) + 0.5) * (2.0 / ny)
+    p = (np.cos(2 * np.pi * (yc + 1.0) / 2.0)[:, None, None] * np.cos(2 * np.pi * z / g.lz)[None, :, None]
+         * np.cos(2 * np.pi * 3 * x / g.lx)[None, None, :])
+    lam = (-(4 / g.dx ** 2) * np.sin(np.pi * 3 / nx) ** 2 - (4 / g.dz ** 2) * np.sin(np.pi / nz) ** 2
+           - (4 / (2.0 / ny) ** 2) * np.sin(np.pi * 2 / (2 * ny)) ** 2)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, pdd_parts=3, device=DEV)
+    got = solve_gpu(P, plan, lam * p)
+    assert np.max(np.abs(got - p)) <= 1e-13
+
+
+def test_fp64_constant_rhs_gives_zero(P):
+    nx, ny, nz = 8, 8, 8
+    plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=P.PP_FP64, device=DEV)
+    got = solve_gpu(P, plan, np.full((ny, nz, nx), 3.0))
+    assert np.max(np.abs(got)) < 1e-13
+
+
+# ------------------------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("walls_zero", [True, False])
+def test_fp64_projection_channel32(P, walls_zero):
+    case = W.CHANNEL_32
+    faces = W.tanh_faces(case.ny, case.stretch)
+    g = oracle.Grid(case.nx, case.nz, faces)
+    u, v, w = W.random_velocity(0, case.nx, case.ny, case.nz, walls_zero=walls_zero)
+    dt = 1e-3
+    want = oracle.project(g, u, v, w, dt)
+    plan = P.Plan(case.nx, case.ny, case.nz, faces, precision=P.PP_FP64, pdd_parts=4, device=DEV)
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    pt = torch.empty(case.ny, case.nz, case.nx, dtype=torch.float64, device=DEV)
+    plan.project(ut, vt, wt, dt, p_out=pt)
+    torch.cuda.synchronize()
+    for got, ref in zip((ut, vt, wt, pt), want):
+        assert relerr(got.cpu().numpy(), ref) <= 1e-12
+    assert np.array_equal(vt[0].cpu().numpy(), v[0]) and np.array_equal(vt[-1].cpu().numpy(), v[-1])
+    if walls_zero:
+        d = oracle.divergence(g, ut.cpu().numpy(), vt.cpu().numpy(), wt.cpu().numpy())
+        assert np.max(np.abs(d)) <= 1e-12 * np.max(np.abs(oracle.divergence(g, u, v, w)))
+
+
+def test_fp64_projection_adjoint_channel(P):
+    nx, ny, nz = 24, 16, 12
+    faces = W.tanh_faces(ny, 1.8)
+    g = oracle.Grid(nx, nz, faces)
+    wu, wv, ww = W.weight_field(4, nx, ny, nz)
+    want = oracle.project_adjoint(g, wu, wv, ww)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, pdd_parts=4, device=DEV)
+    gu, gv, gw = to_dev(wu), to_dev(wv), to_dev(ww)
+    plan.project_adjoint(gu, gv, gw)
+    torch.cuda.synchronize()
+    for got, ref in zip((gu, gv, gw), want):
+        assert relerr(got.cpu().numpy(), ref) <= 1e-12
+
+
+# ------------------------------------------------------------------------------ FP32 forms
+
+@pytest.mark.parametrize("nx,ny,nz,parts", [(32, 32, 32, 4), (96, 48, 64, 1), (64, 96, 48, 2)])
+def test_fp32_solve(P, nx, ny, nz, parts):
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(2, nx, ny, nz))
+    f -= np.einsum("j,jki->", g.dy, f) / (g.dy.sum() * nx * nz)
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32, pdd_parts=parts, fp64_low_modes=4, device=DEV)
+    got = solve_gpu(P, plan, f, dtype=torch.float32)
+    assert relerr(got, want) <= 2e-5
+
+
+@pytest.mark.parametrize("nx,ny,nz,parts,steps,tol", [
+    (32, 32, 32, 4, 1, 2e-9), (96, 48, 64, 2, 1, 2e-9), (64, 96, 48, 4, 2, 1e-12)])
+def test_fp32_refined_solve(P, nx, ny, nz, parts, steps, tol):
+    faces = W.tanh_faces(ny, 2.2)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(2, nx, ny, nz))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=parts, fp64_low_modes=4,
+                  refine_steps=steps, device=DEV)
+    ft = to_dev(f)
+    out = torch.empty_like(ft)
+    plan.solve(ft, out=out)
+    torch.cuda.synchronize()
+    assert relerr(out.cpu().numpy(), want) <= tol
+
+
+def test_fp32_projection_and_adjoint(P):
+    nx, ny, nz = 32, 24, 16
+    faces = W.tanh_faces(ny, 1.8)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.random_velocity(3, nx, ny, nz)
+    want = oracle.project(g, u, v, w, 1e-3)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32, pdd_parts=2, device=DEV)
+    ut, vt, wt = (to_dev(a, torch.float32) for a in (u, v, w))
+    plan.project(ut, vt, wt, 1e-3)
+    for got, ref in zip((ut, vt, wt), want[:3]):
+        assert relerr(got.double().cpu().numpy(), ref) <= 2e-5
+    wts = W.weight_field(4, nx, ny, nz)
+    wantT = oracle.project_adjoint(g, *wts)
+    gt = [to_dev(a, torch.float32) for a in wts]
+    plan.project_adjoint(*gt)
+    for got, ref in zip(gt, wantT):
+        assert relerr(got.double().cpu().numpy(), ref) <= 2e-5
+
+
+# ------------------------------------------------------------------------------ errors
+
+def test_nonfinite_input_sets_device_status(P):
+    nx, ny, nz = 8, 8, 8
+    plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=P.PP_FP64, flags=P.POISSON_CHECK_FINITE,
+                  device=DEV)
+    f = np.zeros((ny, nz, nx))
+    f[3, 2, 1] = np.nan
+    plan.solve(to_dev(f))
+    assert plan.device_status() == 6
+    plan.solve(to_dev(np.ones((ny, nz, nx))))
+    assert plan.device_status() == 0
+
+
+def test_bad_arguments_are_rejected(P):
+    nx, ny, nz = 8, 8, 8
+    plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=P.PP_FP64, device=DEV)
+    with pytest.raises(ValueError):
+        plan.solve(torch.zeros((ny, nz, nx), dtype=torch.float32, device=DEV))
+    from paper_2104_08863_gb300 import _native
+    L = _native.lib()
+    buf = torch.zeros(ny * nz * nx + 1, dtype=torch.float64, device=DEV)
+    mis = buf.data_ptr() + 8     # not 16-byte aligned
+    assert L.poisson_solve(plan._h, mis, mis, torch.cuda.current_stream().cuda_stream) == _native.PS_EINVAL
+    assert L.poisson_solve(plan._h, 0, buf.data_ptr(), 0) == _native.PS_EINVAL
+    assert L.projection_step(plan._h, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 0, -1.0, 0) == \
+        _native.PS_EINVAL
