@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the pressure-projection hot path on GB300.
+
+One step = one projection (Eqs. 4 and 7): the divergence of u* fused into the forward x-FFT,
+the forward z-FFT, the PDD wall-normal solves (P = 8, exact reduced system), the (0, 0) mode,
+the inverse z- and x-FFTs, and the gradient correction, in FP64, on the 512 x 384 x 512
+channel (Lx = 2 pi, Ly = 2, Lz = pi, tanh stretching 2.0).  Input: laminar Poiseuille profile
+plus seeded N(0, 0.1^2) noise (seed 1), no-penetration walls, dt = 1e-4.
+
+Metric: Poisson-solve throughput in Gpts/s (grid points per second of whole projection steps).
+The fields (2.4 GB of velocity, 0.8 GB spectrum) are far larger than the 129 MB L2, so no flush
+is needed between steps.
+
+--impl reference times the CPU oracle (numpy, FP64) on a bounded sample of the same workload.
+Under torchrun every rank runs an independent replica (the path is replicas-only on this pool).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+CASE = W.CHANNEL_512
+PDD_PARTS = 8
+DT = 1e-4
+METRIC = "Poisson solve Gpts/s (FP64 projection step: divergence + FFT/PDD solve + gradient)"
+UNIT = "Gpts/s"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu if isinstance(gpu, int) else (str(gpu) if str(gpu).startswith("GPU-") else f"GPU-{gpu}")
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- roofline model
+def kernel_model(name: str, nx: int, ny: int, nz: int):
+    """Algorithmic HBM bytes and FFT flops of one launch of each FP64 projection kernel.
+
+    N = nx ny nz real points, Ns = (nx/2 + 1) ny nz complex modes (16 bytes each in FP64).
+    FFT flops use the 5 n log2 n convention for an n-point complex transform (2.5 n log2 n
+    for an n-point real transform).
+    """
+    N = nx * ny * nz
+    Ns = (nx // 2 + 1) * ny * nz
+    plane = nx * nz
+    if name == "fwd_x":        # read u, v (ny+1 planes), w; write the half spectrum
+        return 8 * (3 * N + plane) + 16 * Ns, 2.5 * N * math.log2(nx)
+    if name in ("fft_z_fwd", "fft_z_inv"):
+        return 32 * Ns, 5.0 * Ns * math.log2(nz)
+    if name == "tridiag_pdd":
+        return 32 * Ns, 0.0
+    if name == "inv_x":        # read the half spectrum, write p
+        return 16 * Ns + 8 * N, 2.5 * N * math.log2(nx)
+    if name == "gradient":     # read p, u, v, w; write u, v, w
+        return 8 * N + 2 * 8 * (3 * N + plane), 0.0
+    return 0, 0.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP64 FMA throughput measured on this machine's GB300 by a DFMA-throughput microbenchmark:
+# 502 G DFMA/s (1.6 per clock per SM at the 2070 MHz nominal clock) = 1004 GFLOP/s.
+FP64_PEAK_GFLOPS = 1004.0
+
+
+# ------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(seconds: float = 12.0):
+    """Time the CPU oracle's projection on a sample of the workload (same Ny, stretching, dt).
+
+    The sample keeps the wall-normal grid (Ny = 384, tanh 2.0) and shrinks the periodic plane
+    to 64 x 64; the oracle is repeated until about `seconds` have passed.  Returns Gpts/s.
+    """
+    import oracle
+    nx, nz = 64, 64
+    faces = W.tanh_faces(CASE.ny, CASE.stretch)
+    g = oracle.Grid(nx, nz, faces, CASE.lx, CASE.lz)
+    sample = W.ChannelCase("sample", nx, CASE.ny, nz, CASE.stretch)
+    u, v, w = W.poiseuille_plus_noise(1, sample)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.project(g, u, v, w, DT)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    pts = reps * nx * nz * CASE.ny
+    return {"value": pts / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle.project on {nx}x{CASE.ny}x{nz} (same Ny=384 tanh 2.0 wall-normal grid), "
+                      f"{reps} runs in {el:.1f} s, numpy FP64 FFT + extended-precision Thomas, 1 thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        oracle_sample(seconds=1.0)
+    for _ in range(args.steps):
+        steps.append(oracle_sample(seconds=5.0))
+    vals = [s["value"] for s in steps]
+    value = statistics.median(vals)
+    cb = dict(steps[-1])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": CASE.npoints / (value * 1e9) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(),
+           "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def config_dict():
+    return {"workload": f"{CASE.name} FP64 projection step", "grid": [CASE.nx, CASE.ny, CASE.nz],
+            "pdd_parts": PDD_PARTS, "tridiag": "PDD, exact reduced system", "dt": DT,
+            "input": "Poiseuille 1-y^2 + N(0,0.1^2) seed 1, walls v=0",
+            "l2": "no flush: fields 2.4 GB >> 129 MB L2", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2104_08863_gb300 import build as b
+    b.build()
+    import paper_2104_08863_gb300 as P
+
+    faces = W.tanh_faces(CASE.ny, CASE.stretch)
+    plan = P.Plan(CASE.nx, CASE.ny, CASE.nz, faces, CASE.lx, CASE.lz, precision=P.PP_FP64,
+                  tridiag=P.PT_PDD_EXACT, pdd_parts=PDD_PARTS, flags=P.POISSON_TIMING, device=dev)
+    u0, v0, w0 = W.poiseuille_plus_noise(1, CASE)
+    u, v, w = (torch.from_numpy(a).to(dev) for a in (u0, v0, w0))
+    p = torch.empty(CASE.ny, CASE.nz, CASE.nx, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        plan.project(u, v, w, DT, p_out=p)
+    launches_per_step = plan.last_launch_count
+    barrier()
+    clocks = ClockSampler(torch.cuda.get_device_properties(dev).uuid if hasattr(
+        torch.cuda.get_device_properties(dev), "uuid") else local)
+    clocks.start()
+    time.sleep(0.3)
+    stage = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.project(u, v, w, DT, p_out=p)
+        for name, ms in plan.stage_times():
+            stage.setdefault(name, []).append(ms)
+    e1.record(stream)
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * CASE.npoints / (ms_step * 1e-3) / 1e9
+
+    # dominant kernel and its roofline
+    totals = {k: sum(vs) for k, vs in stage.items()}
+    dom = max(totals, key=totals.get)
+    launches = len(stage[dom])
+    avg_ms = totals[dom] / launches
+    nbytes, flops = kernel_model(dom, CASE.nx, CASE.ny, CASE.nz)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
+    if t_alu > t_hbm:
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None, "kernel": dom,
+                "peak_source": "measured FP64 DFMA throughput (2 flops/DFMA)",
+                "hbm_achieved_gbs": nbytes / (avg_ms * 1e-3) / 1e9}
+    else:
+        achieved = nbytes / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["avg_launch_ms"] = avg_ms
+    share = {k: round(v / sum(totals.values()), 4) for k, v in sorted(totals.items(), key=lambda kv: -kv[1])}
+
+    # end to end through the host-buffer C-ABI entry point (pinned host memory)
+    uh, vh, wh = (torch.from_numpy(a).pin_memory() for a in (u0, v0, w0))
+    ph = torch.empty(CASE.ny, CASE.nz, CASE.nx, dtype=torch.float64).pin_memory()
+    staging = (u, v, w, p)
+    plan.project_host(uh, vh, wh, DT, staging, p_h=ph)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.project_host(uh, vh, wh, DT, staging, p_h=ph)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 8 * (3 * CASE.npoints + CASE.nx * CASE.nz)
+    d2h = h2d + 8 * CASE.npoints
+
+    cpu = oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
+               "roofline": roof, "kernel_share": share,
+               "cpu_baseline": cpu,
+               "e2e": {"value": world * CASE.npoints / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+               "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

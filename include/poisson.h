@@ -60,7 +60,8 @@ typedef enum {
   PT_PDD_EXACT = 2        /* PDD with pdd_parts sub-blocks, exact reduced system Eq. 21  */
 } poisson_tridiag;
 
-#define POISSON_CHECK_FINITE 0x1u   /* flag: scan inputs, set PS_ENONFINITE on NaN/Inf */
+#define POISSON_CHECK_FINITE 0x1u   /* flag: scan inputs, set PS_ENONFINITE on NaN/Inf     */
+#define POISSON_TIMING       0x2u   /* flag: record CUDA events around every kernel launch */
 
 typedef struct {
   int nx, ny, nz;           /* cells; nx even, nx/2 and nz of the form 2^a 3^b; ny >= 2 */
@@ -120,6 +121,12 @@ poisson_status poisson_device_status(poisson_plan_t plan, void* stream);
 
 /* Number of kernel launches the last call on this plan issued (for accounting). */
 int poisson_last_launch_count(poisson_plan_t plan);
+
+/* With POISSON_TIMING: device time (ms) of each kernel launch of the last call on this plan,
+ * measured by events recorded on the launching stream.  Writes up to `max` entries of ms[]
+ * and names[] (static strings; either may be NULL), waits for the last event, and returns
+ * the number of launches timed (-1 when timing is off or an event query fails). */
+int poisson_stage_times(poisson_plan_t plan, float* ms, const char** names, int max);
 
 /* Free the host plan (does not touch the caller's workspace). NULL is accepted. */
 poisson_status poisson_plan_destroy(poisson_plan_t plan);

@@ -14,10 +14,10 @@ import torch
 
 from . import _native
 from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_PDD_EXACT,
-                      POISSON_CHECK_FINITE, PoissonError, check)
+                      POISSON_CHECK_FINITE, POISSON_TIMING, PoissonError, check)
 
 __all__ = ["Plan", "ProjectionFn", "PoissonError", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
-           "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "POISSON_CHECK_FINITE"]
+           "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "POISSON_CHECK_FINITE", "POISSON_TIMING"]
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -114,6 +114,15 @@ class Plan:
 
     def device_status(self, stream=None) -> int:
         return int(_native.lib().poisson_device_status(self._h, _stream(stream)))
+
+    def stage_times(self, max_entries: int = 64):
+        """[(kernel name, ms)] of every launch of the last call (needs flags=POISSON_TIMING)."""
+        ms = (ctypes.c_float * max_entries)()
+        names = (ctypes.c_char_p * max_entries)()
+        n = _native.lib().poisson_stage_times(self._h, ms, names, max_entries)
+        if n < 0:
+            raise RuntimeError("stage timing unavailable (plan created without POISSON_TIMING)")
+        return [(names[i].decode(), float(ms[i])) for i in range(min(n, max_entries))]
 
     @property
     def last_launch_count(self) -> int:

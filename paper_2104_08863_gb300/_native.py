@@ -16,12 +16,13 @@ PS_OK, PS_EINVAL, PS_EUNSUPPORTED, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINI
 PP_FP64, PP_FP32, PP_FP32_REFINED = 0, 1, 2
 PT_AUTO, PT_THOMAS, PT_PDD_EXACT = 0, 1, 2
 POISSON_CHECK_FINITE = 0x1
+POISSON_TIMING = 0x2
 
 # Every symbol declared in include/poisson.h.
 EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
     "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
-    "poisson_last_launch_count", "poisson_plan_destroy", "poisson_status_string",
+    "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
 
@@ -64,6 +65,8 @@ def lib() -> ctypes.CDLL:
     L.poisson_device_status.argtypes = [vp, vp]
     L.poisson_last_launch_count.argtypes = [vp]
     L.poisson_last_launch_count.restype = i
+    L.poisson_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p), i]
+    L.poisson_stage_times.restype = i
     L.poisson_plan_destroy.argtypes = [vp]
     L.poisson_status_string.argtypes = [i]
     L.poisson_status_string.restype = ctypes.c_char_p

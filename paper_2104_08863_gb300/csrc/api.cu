@@ -31,6 +31,10 @@ struct poisson_plan_s {
   unsigned char* ws;
   DevTables dt;
   int launches;
+  // POISSON_TIMING: one event pair around every launch of the last call
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char*> ev_names;
+  int nev;
 };
 
 namespace {
@@ -212,6 +216,8 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   pl->ws_bytes = off;
   pl->ws = nullptr;
   pl->launches = 0;
+  pl->nev = 0;
+  pl->nev = 0;
   *out = pl;
   return PS_OK;
 }
@@ -260,11 +266,31 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
 
 namespace {
 
-#define PP_TRY(expr)                                   \
-  do {                                                 \
-    cudaError_t _e = (expr);                           \
-    ++pl->launches;                                    \
-    if (_e != cudaSuccess) return PS_ECUDA;            \
+bool timer_begin(poisson_plan_s* pl, cudaStream_t st) {
+  if (!(pl->flags & POISSON_TIMING)) return false;
+  if (pl->nev >= 64) return false;
+  while ((int)pl->ev.size() < 2 * (pl->nev + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    pl->ev.push_back(e);
+  }
+  return cudaEventRecord(pl->ev[2 * pl->nev], st) == cudaSuccess;
+}
+
+void timer_end(poisson_plan_s* pl, cudaStream_t st, const char* name) {
+  cudaEventRecord(pl->ev[2 * pl->nev + 1], st);
+  if ((int)pl->ev_names.size() <= pl->nev) pl->ev_names.resize(pl->nev + 1);
+  pl->ev_names[pl->nev] = name;
+  ++pl->nev;
+}
+
+#define PP_TRY_N(name, expr)                              \
+  do {                                                    \
+    const bool _t = timer_begin(pl, st);                  \
+    cudaError_t _e = (expr);                              \
+    if (_t) timer_end(pl, st, name);                      \
+    ++pl->launches;                                       \
+    if (_e != cudaSuccess) return PS_ECUDA;               \
   } while (0)
 
 // Spectral middle of a solve on the plan's spectral buffer: forward z-FFT, wall-normal
@@ -275,31 +301,31 @@ poisson_status spectral_core(poisson_plan_s* pl, cplx<T>* spec, cudaStream_t st)
 template <>
 poisson_status spectral_core<double>(poisson_plan_s* pl, cplx<double>* spec, cudaStream_t st) {
   const Geometry& g = pl->g;
-  PP_TRY(launch_fft_z<double>(g, pl->dt, pl->fz, -1, spec, st));
-  PP_TRY((launch_tridiag<double, double>(g, pl->dt, pl->parts, -1, false, spec, st)));
-  PP_TRY(launch_mode00<double>(g, pl->dt, false, spec, st));
-  PP_TRY(launch_fft_z<double>(g, pl->dt, pl->fz, +1, spec, st));
+  PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, pl->dt, pl->fz, -1, spec, st));
+  PP_TRY_N("tridiag_pdd", (launch_tridiag<double, double>(g, pl->dt, pl->parts, -1, false, spec, st)));
+  PP_TRY_N("mode00", launch_mode00<double>(g, pl->dt, false, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, pl->dt, pl->fz, +1, spec, st));
   return PS_OK;
 }
 
 template <>
 poisson_status spectral_core<float>(poisson_plan_s* pl, cplx<float>* spec, cudaStream_t st) {
   const Geometry& g = pl->g;
-  PP_TRY(launch_fft_z<float>(g, pl->dt, pl->fz, -1, spec, st));
-  PP_TRY((launch_tridiag<float, float>(g, pl->dt, pl->parts, pl->low, false, spec, st)));
+  PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, pl->dt, pl->fz, -1, spec, st));
+  PP_TRY_N("tridiag_pdd", (launch_tridiag<float, float>(g, pl->dt, pl->parts, pl->low, false, spec, st)));
   if (pl->low >= 0) {
     cplx<double>* scr = (cplx<double>*)(pl->ws + pl->off_scratch);
-    PP_TRY(launch_tridiag_low64(g, pl->dt, pl->parts, pl->low, spec, scr, st));
+    PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, pl->dt, pl->parts, pl->low, spec, scr, st));
   }
-  PP_TRY(launch_mode00<float>(g, pl->dt, false, spec, st));
-  PP_TRY(launch_fft_z<float>(g, pl->dt, pl->fz, +1, spec, st));
+  PP_TRY_N("mode00", launch_mode00<float>(g, pl->dt, false, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<float>(g, pl->dt, pl->fz, +1, spec, st));
   return PS_OK;
 }
 
 template <typename T, typename TI>
 poisson_status forward_and_core(poisson_plan_s* pl, FwdMode mode, const FwdArgs& args, cudaStream_t st) {
   cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
-  PP_TRY((launch_fwd_x<T, TI>(pl->g, pl->dt, pl->fm, mode, args, spec, st)));
+  PP_TRY_N("fwd_x", (launch_fwd_x<T, TI>(pl->g, pl->dt, pl->fm, mode, args, spec, st)));
   return spectral_core<T>(pl, spec, st);
 }
 
@@ -307,7 +333,7 @@ template <typename T, typename TO>
 poisson_status inverse_x(poisson_plan_s* pl, InvMode mode, TO* out, cudaStream_t st) {
   cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
   const double scale = 1.0 / ((double)pl->g.nx * (double)pl->g.nz);
-  PP_TRY((launch_inv_x<T, TO>(pl->g, pl->dt, pl->fm, mode, spec, out, scale, st)));
+  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(pl->g, pl->dt, pl->fm, mode, spec, out, scale, st)));
   return PS_OK;
 }
 
@@ -317,7 +343,7 @@ size_t vface_count(const poisson_plan_s* pl) { return (size_t)(pl->g.ny + 1) * p
 template <typename T>
 poisson_status check_finite(poisson_plan_s* pl, const void* x, size_t n, cudaStream_t st) {
   if (!(pl->flags & POISSON_CHECK_FINITE)) return PS_OK;
-  PP_TRY(launch_check_finite<T>((const T*)x, n, pl->dt.status, st));
+  PP_TRY_N("check_finite", launch_check_finite<T>((const T*)x, n, pl->dt.status, st));
   return PS_OK;
 }
 
@@ -337,6 +363,7 @@ poisson_status poisson_solve(poisson_plan_t pl, const void* rhs, void* p, void* 
   if (!aligned16(rhs) || !aligned16(p)) return PS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   pl->launches = 0;
+  pl->nev = 0;
   FwdArgs args = {};
   args.in = rhs;
   args.in_scale = 1.0;
@@ -374,6 +401,7 @@ poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, voi
   if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   pl->launches = 0;
+  pl->nev = 0;
   FwdArgs args = {};
   args.u = u; args.v = v; args.w = w;
   args.in_scale = 1.0 / dt;
@@ -382,13 +410,13 @@ poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, voi
     PP_RET(check_finite<double>(pl, u, cell_count(pl), st));
     PP_RET((forward_and_core<double, double>(pl, FWD_DIV, args, st)));
     PP_RET((inverse_x<double, double>(pl, INV_STORE, p, st)));
-    PP_TRY(launch_gradient<double>(pl->g, pl->dt, p, (double*)u, (double*)v, (double*)w, dt, st));
+    PP_TRY_N("gradient", launch_gradient<double>(pl->g, pl->dt, p, (double*)u, (double*)v, (double*)w, dt, st));
   } else {
     float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
     PP_RET(check_finite<float>(pl, u, cell_count(pl), st));
     PP_RET((forward_and_core<float, float>(pl, FWD_DIV, args, st)));
     PP_RET((inverse_x<float, float>(pl, INV_STORE, p, st)));
-    PP_TRY(launch_gradient<float>(pl->g, pl->dt, p, (float*)u, (float*)v, (float*)w, dt, st));
+    PP_TRY_N("gradient", launch_gradient<float>(pl->g, pl->dt, p, (float*)u, (float*)v, (float*)w, dt, st));
   }
   return PS_OK;
 }
@@ -400,6 +428,7 @@ poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, vo
   if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   pl->launches = 0;
+  pl->nev = 0;
   FwdArgs args = {};
   args.u = gu; args.v = gv; args.w = gw;
   args.in_scale = 1.0;
@@ -407,12 +436,12 @@ poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, vo
     double* q = (double*)(pl->ws + pl->off_pbuf);
     PP_RET((forward_and_core<double, double>(pl, FWD_GRADT, args, st)));
     PP_RET((inverse_x<double, double>(pl, INV_STORE, q, st)));
-    PP_TRY(launch_adjoint_epilogue<double>(pl->g, pl->dt, q, (double*)gu, (double*)gv, (double*)gw, st));
+    PP_TRY_N("adj_epilogue", launch_adjoint_epilogue<double>(pl->g, pl->dt, q, (double*)gu, (double*)gv, (double*)gw, st));
   } else {
     float* q = (float*)(pl->ws + pl->off_pbuf);
     PP_RET((forward_and_core<float, float>(pl, FWD_GRADT, args, st)));
     PP_RET((inverse_x<float, float>(pl, INV_STORE, q, st)));
-    PP_TRY(launch_adjoint_epilogue<float>(pl->g, pl->dt, q, (float*)gu, (float*)gv, (float*)gw, st));
+    PP_TRY_N("adj_epilogue", launch_adjoint_epilogue<float>(pl->g, pl->dt, q, (float*)gu, (float*)gv, (float*)gw, st));
   }
   return PS_OK;
 }
@@ -451,7 +480,23 @@ poisson_status poisson_device_status(poisson_plan_t pl, void* stream) {
 
 int poisson_last_launch_count(poisson_plan_t pl) { return pl ? pl->launches : -1; }
 
+int poisson_stage_times(poisson_plan_t pl, float* ms, const char** names, int max) {
+  if (!pl || !(pl->flags & POISSON_TIMING)) return -1;
+  const int n = pl->nev;
+  if (n == 0) return 0;
+  if (cudaEventSynchronize(pl->ev[2 * n - 1]) != cudaSuccess) return -1;
+  for (int i = 0; i < n && i < max; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pl->ev[2 * i], pl->ev[2 * i + 1]) != cudaSuccess) return -1;
+    if (ms) ms[i] = t;
+    if (names) names[i] = pl->ev_names[i];
+  }
+  return n;
+}
+
 poisson_status poisson_plan_destroy(poisson_plan_t pl) {
+  if (pl)
+    for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   delete pl;
   return PS_OK;
 }
