@@ -115,6 +115,25 @@ poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_h
                                     void* w_host, void* p_host, void* u_dev, void* v_dev,
                                     void* w_dev, void* p_dev, double dt, void* stream);
 
+/* Capacity of the library's built-in device workspace used by poisson_solve_static_ws. */
+#define POISSON_STATIC_WS_MAX_BYTES (8u * 1024u * 1024u)
+
+/* poisson_solve without caller-provided workspace, for callers that cannot allocate device
+ * memory when they solve (a host application whose memory pool owns the device and forbids
+ * library allocations, or a time-critical loop that must not pay cudaMalloc's latency and
+ * implicit synchronisation).  The paper has no counterpart: this is a deployment variant.
+ * Same arguments, precisions and results as poisson_solve on `plan` (which must have been
+ * created by poisson_plan_create; poisson_set_workspace is not needed).  The workspace is a
+ * fixed device array of POISSON_STATIC_WS_MAX_BYTES inside the library, held by every GPU
+ * that loads the library until the process exits; plans whose poisson_workspace_size exceeds
+ * it are rejected with PS_EUNSUPPORTED.  No cudaMalloc, cudaFree or other allocator is
+ * called.  The first call on each device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  Every call reloads
+ * the plan's tables into the array and clears its status word; all calls share the one array
+ * per device, so calls that overlap on the GPU (different streams, threads or plans) race:
+ * serialise them. */
+poisson_status poisson_solve_static_ws(poisson_plan_t plan, const void* rhs, void* p, void* stream);
+
 /* Synchronise `stream` and read the device status word (PS_OK, PS_ENONFINITE, ...),
  * then clear it. */
 poisson_status poisson_device_status(poisson_plan_t plan, void* stream);

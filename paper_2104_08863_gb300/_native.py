@@ -15,13 +15,14 @@ LIB_PATH = os.path.join(HERE, "libpoisson.so")
 PS_OK, PS_EINVAL, PS_EUNSUPPORTED, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ENOWORKSPACE = range(8)
 PP_FP64, PP_FP32, PP_FP32_REFINED = 0, 1, 2
 PT_AUTO, PT_THOMAS, PT_PDD_EXACT = 0, 1, 2
+POISSON_STATIC_WS_MAX_BYTES = 8 * 1024 * 1024
 POISSON_CHECK_FINITE = 0x1
 POISSON_TIMING = 0x2
 
 # Every symbol declared in include/poisson.h.
 EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
-    "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
+    "poisson_solve_static_ws", "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
     "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
@@ -59,6 +60,7 @@ def lib() -> ctypes.CDLL:
     L.poisson_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.poisson_set_workspace.argtypes = [vp, vp, sz, vp]
     L.poisson_solve.argtypes = [vp, vp, vp, vp]
+    L.poisson_solve_static_ws.argtypes = [vp, vp, vp, vp]
     L.projection_step.argtypes = [vp, vp, vp, vp, vp, d, vp]
     L.projection_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
     L.projection_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, vp]
@@ -71,6 +73,7 @@ def lib() -> ctypes.CDLL:
     L.poisson_status_string.argtypes = [i]
     L.poisson_status_string.restype = ctypes.c_char_p
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
+                 "poisson_solve_static_ws",
                  "projection_step", "projection_step_adjoint", "projection_step_host",
                  "poisson_device_status", "poisson_plan_destroy"):
         getattr(L, name).restype = i

@@ -17,25 +17,7 @@
 
 using namespace pp;
 
-struct poisson_plan_s {
-  Geometry g;
-  double lx, lz;
-  int precision, tridiag, parts, low, refine;
-  unsigned flags;
-  FftFactors fm, fz;
-  std::vector<double> faces, dy, h, a, c, lamx, lamz;
-  std::vector<unsigned char> host_tables;   // staging image of the device tables
-  // workspace layout (byte offsets)
-  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, ws_bytes;
-  size_t tab_offsets[32];
-  unsigned char* ws;
-  DevTables dt;
-  int launches;
-  // POISSON_TIMING: one event pair around every launch of the last call
-  std::vector<cudaEvent_t> ev;
-  std::vector<const char*> ev_names;
-  int nev;
-};
+// struct poisson_plan_s is defined in internal.h (shared with the static-workspace entry point).
 
 namespace {
 

@@ -94,3 +94,24 @@ template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st);
 
 }  // namespace pp
+
+// Host plan (opaque to callers of include/poisson.h).
+struct poisson_plan_s {
+  pp::Geometry g;
+  double lx, lz;
+  int precision, tridiag, parts, low, refine;
+  unsigned flags;
+  pp::FftFactors fm, fz;
+  std::vector<double> faces, dy, h, a, c, lamx, lamz;
+  std::vector<unsigned char> host_tables;   // staging image of the device tables
+  // workspace layout (byte offsets)
+  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, ws_bytes;
+  size_t tab_offsets[32];
+  unsigned char* ws;
+  pp::DevTables dt;
+  int launches;
+  // POISSON_TIMING: one event pair around every launch of the last call
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char*> ev_names;
+  int nev;
+};
