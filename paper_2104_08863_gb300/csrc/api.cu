@@ -62,6 +62,31 @@ bool spec_is_fp64(const poisson_plan_s* pl) { return pl->precision == PP_FP64; }
 
 }  // namespace
 
+namespace pp {
+DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
+  DevTables dt;
+  unsigned char* tb = base + pl->off_tables;
+  const size_t* to = pl->tab_offsets;
+  dt.d.tw_m = (const cplx<double>*)(tb + to[0]);
+  dt.d.tw_post = (const cplx<double>*)(tb + to[1]);
+  dt.d.tw_z = (const cplx<double>*)(tb + to[2]);
+  dt.d.a = (const double*)(tb + to[3]);
+  dt.d.c = (const double*)(tb + to[4]);
+  dt.f.tw_m = (const cplx<float>*)(tb + to[5]);
+  dt.f.tw_post = (const cplx<float>*)(tb + to[6]);
+  dt.f.tw_z = (const cplx<float>*)(tb + to[7]);
+  dt.f.a = (const float*)(tb + to[8]);
+  dt.f.c = (const float*)(tb + to[9]);
+  dt.lamx = (const double*)(tb + to[10]);
+  dt.lamz = (const double*)(tb + to[11]);
+  dt.dy = (const double*)(tb + to[12]);
+  dt.h = (const double*)(tb + to[13]);
+  dt.status = (int*)(base + pl->off_status);
+  dt.acc = (double*)(base + pl->off_acc);
+  return dt;
+}
+}  // namespace pp
+
 extern "C" {
 
 const char* poisson_status_string(poisson_status s) {
@@ -195,6 +220,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   if (L >= 0) off = align_up(off + 16 * (size_t)ny * (L + 1) * (2 * L + 1), 256);
   pl->off_tables = off; off = align_up(off + tab_bytes, 256);
   pl->off_status = off; off = align_up(off + 256, 256);
+  pl->off_acc = off;    off = align_up(off + 256, 256);
   pl->ws_bytes = off;
   pl->ws = nullptr;
   pl->launches = 0;
@@ -223,24 +249,7 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
   // The host image must outlive the copy; synchronise once here (set-up, not the hot path).
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return PS_ECUDA;
   pl->ws = base;
-  unsigned char* tb = base + pl->off_tables;
-  const size_t* to = pl->tab_offsets;
-  DevTables& dt = pl->dt;
-  dt.d.tw_m = (const cplx<double>*)(tb + to[0]);
-  dt.d.tw_post = (const cplx<double>*)(tb + to[1]);
-  dt.d.tw_z = (const cplx<double>*)(tb + to[2]);
-  dt.d.a = (const double*)(tb + to[3]);
-  dt.d.c = (const double*)(tb + to[4]);
-  dt.f.tw_m = (const cplx<float>*)(tb + to[5]);
-  dt.f.tw_post = (const cplx<float>*)(tb + to[6]);
-  dt.f.tw_z = (const cplx<float>*)(tb + to[7]);
-  dt.f.a = (const float*)(tb + to[8]);
-  dt.f.c = (const float*)(tb + to[9]);
-  dt.lamx = (const double*)(tb + to[10]);
-  dt.lamz = (const double*)(tb + to[11]);
-  dt.dy = (const double*)(tb + to[12]);
-  dt.h = (const double*)(tb + to[13]);
-  dt.status = (int*)(base + pl->off_status);
+  pl->dt = pp::bind_tables(pl, base);
   return PS_OK;
 }
 
@@ -248,19 +257,29 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
 
 namespace {
 
-bool timer_begin(poisson_plan_s* pl, cudaStream_t st) {
-  if (!(pl->flags & POISSON_TIMING)) return false;
-  if (pl->nev >= 64) return false;
+// Execution context of one call: the plan, the workspace it runs on and its table pointers.
+struct Exec {
+  poisson_plan_s* pl;
+  unsigned char* ws;
+  DevTables dt;
+  cudaStream_t st;
+  bool timing;
+};
+
+bool timer_begin(Exec& ex) {
+  poisson_plan_s* pl = ex.pl;
+  if (!ex.timing || pl->nev >= 64) return false;
   while ((int)pl->ev.size() < 2 * (pl->nev + 1)) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return false;
     pl->ev.push_back(e);
   }
-  return cudaEventRecord(pl->ev[2 * pl->nev], st) == cudaSuccess;
+  return cudaEventRecord(pl->ev[2 * pl->nev], ex.st) == cudaSuccess;
 }
 
-void timer_end(poisson_plan_s* pl, cudaStream_t st, const char* name) {
-  cudaEventRecord(pl->ev[2 * pl->nev + 1], st);
+void timer_end(Exec& ex, const char* name) {
+  poisson_plan_s* pl = ex.pl;
+  cudaEventRecord(pl->ev[2 * pl->nev + 1], ex.st);
   if ((int)pl->ev_names.size() <= pl->nev) pl->ev_names.resize(pl->nev + 1);
   pl->ev_names[pl->nev] = name;
   ++pl->nev;
@@ -268,68 +287,12 @@ void timer_end(poisson_plan_s* pl, cudaStream_t st, const char* name) {
 
 #define PP_TRY_N(name, expr)                              \
   do {                                                    \
-    const bool _t = timer_begin(pl, st);                  \
+    const bool _t = timer_begin(ex);                      \
     cudaError_t _e = (expr);                              \
-    if (_t) timer_end(pl, st, name);                      \
-    ++pl->launches;                                       \
+    if (_t) timer_end(ex, name);                          \
+    ++ex.pl->launches;                                    \
     if (_e != cudaSuccess) return PS_ECUDA;               \
   } while (0)
-
-// Spectral middle of a solve on the plan's spectral buffer: forward z-FFT, wall-normal
-// systems, (0, 0) mode, inverse z-FFT.
-template <typename T>
-poisson_status spectral_core(poisson_plan_s* pl, cplx<T>* spec, cudaStream_t st);
-
-template <>
-poisson_status spectral_core<double>(poisson_plan_s* pl, cplx<double>* spec, cudaStream_t st) {
-  const Geometry& g = pl->g;
-  PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, pl->dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", (launch_tridiag<double, double>(g, pl->dt, pl->parts, -1, false, spec, st)));
-  PP_TRY_N("mode00", launch_mode00<double>(g, pl->dt, false, spec, st));
-  PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, pl->dt, pl->fz, +1, spec, st));
-  return PS_OK;
-}
-
-template <>
-poisson_status spectral_core<float>(poisson_plan_s* pl, cplx<float>* spec, cudaStream_t st) {
-  const Geometry& g = pl->g;
-  PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, pl->dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", (launch_tridiag<float, float>(g, pl->dt, pl->parts, pl->low, false, spec, st)));
-  if (pl->low >= 0) {
-    cplx<double>* scr = (cplx<double>*)(pl->ws + pl->off_scratch);
-    PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, pl->dt, pl->parts, pl->low, spec, scr, st));
-  }
-  PP_TRY_N("mode00", launch_mode00<float>(g, pl->dt, false, spec, st));
-  PP_TRY_N("fft_z_inv", launch_fft_z<float>(g, pl->dt, pl->fz, +1, spec, st));
-  return PS_OK;
-}
-
-template <typename T, typename TI>
-poisson_status forward_and_core(poisson_plan_s* pl, FwdMode mode, const FwdArgs& args, cudaStream_t st) {
-  cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
-  PP_TRY_N("fwd_x", (launch_fwd_x<T, TI>(pl->g, pl->dt, pl->fm, mode, args, spec, st)));
-  return spectral_core<T>(pl, spec, st);
-}
-
-template <typename T, typename TO>
-poisson_status inverse_x(poisson_plan_s* pl, InvMode mode, TO* out, cudaStream_t st) {
-  cplx<T>* spec = (cplx<T>*)(pl->ws + pl->off_spec);
-  const double scale = 1.0 / ((double)pl->g.nx * (double)pl->g.nz);
-  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(pl->g, pl->dt, pl->fm, mode, spec, out, scale, st)));
-  return PS_OK;
-}
-
-size_t cell_count(const poisson_plan_s* pl) { return (size_t)pl->g.ny * pl->g.nz * pl->g.nx; }
-size_t vface_count(const poisson_plan_s* pl) { return (size_t)(pl->g.ny + 1) * pl->g.nz * pl->g.nx; }
-
-template <typename T>
-poisson_status check_finite(poisson_plan_s* pl, const void* x, size_t n, cudaStream_t st) {
-  if (!(pl->flags & POISSON_CHECK_FINITE)) return PS_OK;
-  PP_TRY_N("check_finite", launch_check_finite<T>((const T*)x, n, pl->dt.status, st));
-  return PS_OK;
-}
-
-}  // namespace
 
 #define PP_RET(expr)                     \
   do {                                   \
@@ -337,41 +300,127 @@ poisson_status check_finite(poisson_plan_s* pl, const void* x, size_t n, cudaStr
     if (_s != PS_OK) return _s;          \
   } while (0)
 
+// Spectral middle of a solve on the spectral buffer: forward z-FFT, wall-normal systems,
+// (0, 0) mode, inverse z-FFT.
+template <typename T>
+poisson_status spectral_core(Exec& ex, cplx<T>* spec, GaugeMode gauge);
+
+template <>
+poisson_status spectral_core<double>(Exec& ex, cplx<double>* spec, GaugeMode gauge) {
+  const poisson_plan_s* pl = ex.pl;
+  const Geometry& g = pl->g;
+  cudaStream_t st = ex.st;
+  PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, ex.dt, pl->fz, -1, spec, st));
+  PP_TRY_N("tridiag_pdd", (launch_tridiag<double, double>(g, ex.dt, pl->parts, -1, false, spec, st)));
+  PP_TRY_N("mode00", launch_mode00<double>(g, ex.dt, gauge, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, ex.dt, pl->fz, +1, spec, st));
+  return PS_OK;
+}
+
+template <>
+poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge) {
+  const poisson_plan_s* pl = ex.pl;
+  const Geometry& g = pl->g;
+  cudaStream_t st = ex.st;
+  PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
+  PP_TRY_N("tridiag_pdd", (launch_tridiag<float, float>(g, ex.dt, pl->parts, pl->low, false, spec, st)));
+  if (pl->low >= 0) {
+    cplx<double>* scr = (cplx<double>*)(ex.ws + pl->off_scratch);
+    PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, st));
+  }
+  PP_TRY_N("mode00", launch_mode00<float>(g, ex.dt, gauge, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<float>(g, ex.dt, pl->fz, +1, spec, st));
+  return PS_OK;
+}
+
+template <typename T, typename TI>
+poisson_status forward_and_core(Exec& ex, FwdMode mode, const FwdArgs& args, GaugeMode gauge) {
+  cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
+  cudaStream_t st = ex.st;
+  PP_TRY_N("fwd_x", (launch_fwd_x<T, TI>(ex.pl->g, ex.dt, ex.pl->fm, mode, args, spec, st)));
+  return spectral_core<T>(ex, spec, gauge);
+}
+
+template <typename T, typename TO>
+poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate) {
+  cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
+  const double scale = 1.0 / ((double)ex.pl->g.nx * (double)ex.pl->g.nz);
+  cudaStream_t st = ex.st;
+  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st)));
+  return PS_OK;
+}
+
+size_t cell_count(const poisson_plan_s* pl) { return (size_t)pl->g.ny * pl->g.nz * pl->g.nx; }
+size_t vface_count(const poisson_plan_s* pl) { return (size_t)(pl->g.ny + 1) * pl->g.nz * pl->g.nx; }
+
+template <typename T>
+poisson_status check_finite(Exec& ex, const void* x, size_t n) {
+  if (!(ex.pl->flags & POISSON_CHECK_FINITE)) return PS_OK;
+  cudaStream_t st = ex.st;
+  PP_TRY_N("check_finite", launch_check_finite<T>((const T*)x, n, ex.dt.status, st));
+  return PS_OK;
+}
+
+// The solve of poisson_solve on any workspace (caller-owned or the library's static one).
+//
+// PP_FP32_REFINED: p_0 = S32 f; then refine_steps times  r = (f - <f>) - L_h p  (FP64),
+// p += S32 r.  <f> is taken from the first solve's (0, 0) mode so that the FP32 transform of
+// r carries no large constant; the weighted sum of p is accumulated by every inverse pass and
+// each correction's (0, 0) mode cancels it, so the gauge error of the FP32 transforms does not
+// persist (the residual cannot see a constant).
+poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
+  const poisson_plan_s* pl = ex.pl;
+  FwdArgs args = {};
+  args.in = rhs;
+  args.in_scale = 1.0;
+  if (pl->precision == PP_FP64) {
+    PP_RET(check_finite<double>(ex, rhs, cell_count(pl)));
+    PP_RET((forward_and_core<double, double>(ex, FWD_PLAIN, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<double, double>(ex, INV_STORE, (double*)p, false)));
+  } else if (pl->precision == PP_FP32) {
+    PP_RET(check_finite<float>(ex, rhs, cell_count(pl)));
+    PP_RET((forward_and_core<float, float>(ex, FWD_PLAIN, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<float, float>(ex, INV_STORE, (float*)p, false)));
+  } else {
+    PP_RET(check_finite<double>(ex, rhs, cell_count(pl)));
+    if (cudaMemsetAsync(ex.dt.acc, 0, 2 * sizeof(double), ex.st) != cudaSuccess) return PS_ECUDA;
+    PP_RET((forward_and_core<float, double>(ex, FWD_PLAIN, args, GAUGE_STORE_MEAN)));
+    PP_RET((inverse_x<float, double>(ex, INV_STORE, (double*)p, true)));
+    for (int r = 0; r < pl->refine; ++r) {
+      FwdArgs ra = {};
+      ra.in = rhs;
+      ra.p = p;
+      ra.in_scale = 1.0;
+      PP_RET((forward_and_core<float, double>(ex, FWD_RESID, ra, GAUGE_OFFSET)));
+      PP_RET((inverse_x<float, double>(ex, INV_ACCUM, (double*)p, true)));
+    }
+  }
+  return PS_OK;
+}
+
+}  // namespace
+
+namespace pp {
+poisson_status solve_on_workspace(poisson_plan_s* pl, unsigned char* ws, const DevTables& dt, const void* rhs,
+                                  void* p, cudaStream_t st) {
+  Exec ex{pl, ws, dt, st, false};
+  pl->launches = 0;
+  pl->nev = 0;
+  return solve_impl(ex, rhs, p);
+}
+}  // namespace pp
+
 extern "C" {
 
 poisson_status poisson_solve(poisson_plan_t pl, const void* rhs, void* p, void* stream) {
   if (!pl || !rhs || !p) return PS_EINVAL;
   if (!pl->ws) return PS_ENOWORKSPACE;
   if (!aligned16(rhs) || !aligned16(p)) return PS_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+  if (pl->precision == PP_FP32_REFINED && rhs == p) return PS_EINVAL;  // the residual re-reads rhs
   pl->launches = 0;
   pl->nev = 0;
-  FwdArgs args = {};
-  args.in = rhs;
-  args.in_scale = 1.0;
-  if (pl->precision == PP_FP64) {
-    PP_RET(check_finite<double>(pl, rhs, cell_count(pl), st));
-    PP_RET((forward_and_core<double, double>(pl, FWD_PLAIN, args, st)));
-    PP_RET((inverse_x<double, double>(pl, INV_STORE, (double*)p, st)));
-  } else if (pl->precision == PP_FP32) {
-    PP_RET(check_finite<float>(pl, rhs, cell_count(pl), st));
-    PP_RET((forward_and_core<float, float>(pl, FWD_PLAIN, args, st)));
-    PP_RET((inverse_x<float, float>(pl, INV_STORE, (float*)p, st)));
-  } else {
-    if (rhs == p) return PS_EINVAL;   // the residual re-reads rhs after p is written
-    PP_RET(check_finite<double>(pl, rhs, cell_count(pl), st));
-    PP_RET((forward_and_core<float, double>(pl, FWD_PLAIN, args, st)));
-    PP_RET((inverse_x<float, double>(pl, INV_STORE, (double*)p, st)));
-    for (int r = 0; r < pl->refine; ++r) {
-      FwdArgs ra = {};
-      ra.in = rhs;
-      ra.p = p;
-      ra.in_scale = 1.0;
-      PP_RET((forward_and_core<float, double>(pl, FWD_RESID, ra, st)));
-      PP_RET((inverse_x<float, double>(pl, INV_ACCUM, (double*)p, st)));
-    }
-  }
-  return PS_OK;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  return solve_impl(ex, rhs, p);
 }
 
 poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, void* p_out, double dt,
@@ -381,24 +430,25 @@ poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, voi
   if (!(dt > 0.0) || !isfinite(dt)) return PS_EINVAL;
   if (!aligned16(u) || !aligned16(v) || !aligned16(w) || (p_out && !aligned16(p_out))) return PS_EINVAL;
   if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
-  cudaStream_t st = (cudaStream_t)stream;
   pl->launches = 0;
   pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  cudaStream_t st = ex.st;
   FwdArgs args = {};
   args.u = u; args.v = v; args.w = w;
   args.in_scale = 1.0 / dt;
   if (pl->precision == PP_FP64) {
     double* p = p_out ? (double*)p_out : (double*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<double>(pl, u, cell_count(pl), st));
-    PP_RET((forward_and_core<double, double>(pl, FWD_DIV, args, st)));
-    PP_RET((inverse_x<double, double>(pl, INV_STORE, p, st)));
-    PP_TRY_N("gradient", launch_gradient<double>(pl->g, pl->dt, p, (double*)u, (double*)v, (double*)w, dt, st));
+    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+    PP_RET((forward_and_core<double, double>(ex, FWD_DIV, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<double, double>(ex, INV_STORE, p, false)));
+    PP_TRY_N("gradient", launch_gradient<double>(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, st));
   } else {
     float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<float>(pl, u, cell_count(pl), st));
-    PP_RET((forward_and_core<float, float>(pl, FWD_DIV, args, st)));
-    PP_RET((inverse_x<float, float>(pl, INV_STORE, p, st)));
-    PP_TRY_N("gradient", launch_gradient<float>(pl->g, pl->dt, p, (float*)u, (float*)v, (float*)w, dt, st));
+    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
+    PP_RET((forward_and_core<float, float>(ex, FWD_DIV, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<float, float>(ex, INV_STORE, p, false)));
+    PP_TRY_N("gradient", launch_gradient<float>(pl->g, ex.dt, p, (float*)u, (float*)v, (float*)w, dt, st));
   }
   return PS_OK;
 }
@@ -408,22 +458,25 @@ poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, vo
   if (!pl->ws) return PS_ENOWORKSPACE;
   if (!aligned16(gu) || !aligned16(gv) || !aligned16(gw)) return PS_EINVAL;
   if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
-  cudaStream_t st = (cudaStream_t)stream;
   pl->launches = 0;
   pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  cudaStream_t st = ex.st;
   FwdArgs args = {};
   args.u = gu; args.v = gv; args.w = gw;
   args.in_scale = 1.0;
   if (pl->precision == PP_FP64) {
     double* q = (double*)(pl->ws + pl->off_pbuf);
-    PP_RET((forward_and_core<double, double>(pl, FWD_GRADT, args, st)));
-    PP_RET((inverse_x<double, double>(pl, INV_STORE, q, st)));
-    PP_TRY_N("adj_epilogue", launch_adjoint_epilogue<double>(pl->g, pl->dt, q, (double*)gu, (double*)gv, (double*)gw, st));
+    PP_RET((forward_and_core<double, double>(ex, FWD_GRADT, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<double, double>(ex, INV_STORE, q, false)));
+    PP_TRY_N("adj_epilogue",
+             launch_adjoint_epilogue<double>(pl->g, ex.dt, q, (double*)gu, (double*)gv, (double*)gw, st));
   } else {
     float* q = (float*)(pl->ws + pl->off_pbuf);
-    PP_RET((forward_and_core<float, float>(pl, FWD_GRADT, args, st)));
-    PP_RET((inverse_x<float, float>(pl, INV_STORE, q, st)));
-    PP_TRY_N("adj_epilogue", launch_adjoint_epilogue<float>(pl->g, pl->dt, q, (float*)gu, (float*)gv, (float*)gw, st));
+    PP_RET((forward_and_core<float, float>(ex, FWD_GRADT, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<float, float>(ex, INV_STORE, q, false)));
+    PP_TRY_N("adj_epilogue",
+             launch_adjoint_epilogue<float>(pl->g, ex.dt, q, (float*)gu, (float*)gv, (float*)gw, st));
   }
   return PS_OK;
 }

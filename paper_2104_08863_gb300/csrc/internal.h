@@ -27,6 +27,7 @@ struct DevTables {
   const double* dy;        // cell heights dy_j
   const double* h;         // centre distances across face j (j = 1..ny-1; h[0], h[ny] = 0)
   int* status;             // device status word
+  double* acc;             // accumulators of the refined solve: [0] <f>, [1] sum_jki dy_j p_jki
 };
 
 struct Geometry {
@@ -55,9 +56,10 @@ template <typename T, typename TI>
 cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, FwdMode mode,
                          const FwdArgs& args, cplx<T>* spec, cudaStream_t st);
 
+// accumulate: also add sum_jki dy_j out_jki (of this pass's contribution) to tb.acc[1].
 template <typename T, typename TO>
 cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
-                         const cplx<T>* spec, TO* out, double scale, cudaStream_t st);
+                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
@@ -78,8 +80,12 @@ cudaError_t launch_tridiag<float, float>(const Geometry& g, const DevTables& tb,
 cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                  cplx<float>* spec, cplx<double>* scratch, cudaStream_t st);
 
+// Gauge modes of the (0, 0) solve: plain zero weighted mean; GAUGE_STORE_MEAN also stores the
+// rhs mean <f> in tb.acc[0]; GAUGE_OFFSET shifts the result so that the running pressure
+// total (weighted sum tb.acc[1]) plus this correction has zero weighted mean.
+enum GaugeMode { GAUGE_ZERO = 0, GAUGE_STORE_MEAN = 1, GAUGE_OFFSET = 2 };
 template <typename TD>
-cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, bool transposed_gauge, cplx<TD>* spec,
+cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, GaugeMode gauge, cplx<TD>* spec,
                           cudaStream_t st);
 
 template <typename T>
@@ -105,7 +111,7 @@ struct poisson_plan_s {
   std::vector<double> faces, dy, h, a, c, lamx, lamz;
   std::vector<unsigned char> host_tables;   // staging image of the device tables
   // workspace layout (byte offsets)
-  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, ws_bytes;
+  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, off_acc, ws_bytes;
   size_t tab_offsets[32];
   unsigned char* ws;
   pp::DevTables dt;
@@ -115,3 +121,11 @@ struct poisson_plan_s {
   std::vector<const char*> ev_names;
   int nev;
 };
+
+namespace pp {
+// Table pointers of a plan inside a workspace that starts at `base`.
+DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base);
+// poisson_solve's pipeline on an explicit workspace (no timing events).
+poisson_status solve_on_workspace(poisson_plan_s* pl, unsigned char* ws, const DevTables& dt, const void* rhs,
+                                  void* p, cudaStream_t st);
+}  // namespace pp

@@ -68,10 +68,13 @@ __device__ __forceinline__ void gradT_pair(const Geometry& g, const TI* __restri
   f1 = ((u1 - u2) * inv_dx + (w0[i0 + 1] - w1[i0 + 1]) * inv_dz + ty1) * inv_dy;
 }
 
-// f - L_h p at cells (j,k,i0), (j,k,i0+1), FP64 (refinement residual).
+// (f - <f>) - L_h p at cells (j,k,i0), (j,k,i0+1), FP64 (refinement residual).  Removing the
+// mean of f here keeps the FP32 transform of the residual free of a large constant whose
+// rounding noise would otherwise leak into the weakly damped low modes at every step.
 __device__ __forceinline__ void residual_pair(const Geometry& g, const double* __restrict__ f,
                                               const double* __restrict__ p, int j, int k, int i0, double idx2,
-                                              double idz2, double aj, double cj, double& r0, double& r1) {
+                                              double idz2, double aj, double cj, double fmean, double& r0,
+                                              double& r1) {
   const size_t nx = g.nx;
   const size_t row = ((size_t)j * g.nz + k) * nx;
   const double* pr = p + row;
@@ -92,8 +95,8 @@ __device__ __forceinline__ void residual_pair(const Geometry& g, const double* _
     l0 += cj * (pu[i0] - p0);
     l1 += cj * (pu[i0 + 1] - p1);
   }
-  r0 = f[row + i0] - l0;
-  r1 = f[row + i0 + 1] - l1;
+  r0 = (f[row + i0] - fmean) - l0;
+  r1 = (f[row + i0 + 1] - fmean) - l1;
 }
 
 template <typename T, typename TI, int MODE>
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, FwdArgs args, Tables<
         double r0, r1;
         const double idx2 = 1.0 / (g.dx * g.dx), idz2 = 1.0 / (g.dz * g.dz);
         residual_pair(g, reinterpret_cast<const double*>(args.in), reinterpret_cast<const double*>(args.p), j, k,
-                      i0, idx2, idz2, tb.d.a[j], tb.d.c[j], r0, r1);
+                      i0, idx2, idz2, tb.d.a[j], tb.d.c[j], tb.acc[0], r0, r1);
         z = mk<T>(T(r0), T(r1));
       }
     }
@@ -159,10 +162,28 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, FwdArgs args, Tables<
   }
 }
 
-template <typename T, typename TO, int MODE>
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+// Compensated accumulation (s, c) += x.
+__device__ __forceinline__ void acc_add(float& s, float& c, float x) {
+  float e;
+  two_sum(s, x, s, e);
+  c += e;
+}
+__device__ __forceinline__ void acc_add(double& s, double& c, double x) {
+  s += x;
+  (void)c;
+}
+
+template <typename T, typename TO, int MODE, bool ACC>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, Tables<T> tt, FftFactors fm,
                                                const cplx<T>* __restrict__ spec, TO* __restrict__ out, double scl,
-                                               int lpb, int nlines) {
+                                               int lpb, int nlines, const double* __restrict__ dy,
+                                               double* __restrict__ acc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = fm.L;
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -190,20 +211,47 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, Tables<T> tt, FftFact
   __syncthreads();
   cplx<T>* res = fft_smem<T, 1>(buf0, buf1, fm, lpb, 1, M, false, tt.tw_m);
   const T s = T(scl);
-  for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
-    const int t = idx / M, n = idx - t * M;
+  // Epilogue: one warp per line, so each line's weighted sum can be reduced in the warp.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  double wsum = 0.0;
+  for (int t = warp; t < lpb; t += nwarps) {
     const int line = line0 + t;
-    if (line >= nlines) continue;
-    const cplx<T> z = res[idx];
-    TO* o = out + (size_t)line * g.nx + 2 * n;
-    if (MODE == INV_ACCUM) {
-      TO a, b;
-      RealIO<TO>::load2(o, a, b);
-      RealIO<TO>::store2(o, a + TO(z.x * s), b + TO(z.y * s));
-    } else {
-      RealIO<TO>::store2(o, TO(z.x * s), TO(z.y * s));
+    if (line >= nlines) break;
+    T hs = T(0), hc = T(0);
+    for (int n = lane; n < M; n += 32) {
+      const cplx<T> z = res[t * M + n];
+      const T x0 = z.x * s, x1 = z.y * s;
+      TO* o = out + (size_t)line * g.nx + 2 * n;
+      if (MODE == INV_ACCUM) {
+        TO a, b;
+        RealIO<TO>::load2(o, a, b);
+        RealIO<TO>::store2(o, a + TO(x0), b + TO(x1));
+      } else {
+        RealIO<TO>::store2(o, TO(x0), TO(x1));
+      }
+      if (ACC) {
+        acc_add(hs, hc, x0);
+        acc_add(hs, hc, x1);
+      }
+    }
+    if (ACC) {
+      // compensated warp reduction of (hs, hc)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T os = __shfl_xor_sync(0xffffffffu, hs, o), oc = __shfl_xor_sync(0xffffffffu, hc, o);
+        T e;
+        if constexpr (sizeof(T) == 4) {
+          two_sum(hs, os, hs, e);
+        } else {
+          hs += os;
+          e = T(0);
+        }
+        hc += oc + e;
+      }
+      if (lane == 0) wsum += dy[line / g.nz] * ((double)hs + (double)hc);
     }
   }
+  if (ACC && lane == 0 && wsum != 0.0) atomicAdd(acc + 1, wsum);
 }
 
 template <typename T, int SIGN>
@@ -272,21 +320,24 @@ cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactor
 
 template <typename T, typename TO>
 cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
-                         const cplx<T>* spec, TO* out, double scale, cudaStream_t st) {
+                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
   const int nlines = g.ny * g.nz;
   const int lpb = lines_per_cta(fm.L);
   const size_t smem = 2 * (size_t)lpb * fm.L * sizeof(cplx<T>);
   const dim3 grid((nlines + lpb - 1) / lpb);
   cudaError_t e;
-  if (mode == INV_ACCUM) {
-    auto kern = k_inv_x<T, TO, INV_ACCUM>;
-    if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 256, smem, st>>>(g, tabs<T>(tb), fm, spec, out, scale, lpb, nlines);
-  } else {
-    auto kern = k_inv_x<T, TO, INV_STORE>;
-    if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 256, smem, st>>>(g, tabs<T>(tb), fm, spec, out, scale, lpb, nlines);
+#define PP_INV(MODEV, ACCV)                                                                               \
+  {                                                                                                       \
+    auto kern = k_inv_x<T, TO, MODEV, ACCV>;                                                              \
+    if ((e = prep(kern, smem)) != cudaSuccess) return e;                                                  \
+    kern<<<grid, 256, smem, st>>>(g, tabs<T>(tb), fm, spec, out, scale, lpb, nlines, tb.dy, tb.acc);     \
   }
+  if (mode == INV_ACCUM) {
+    if (accumulate) PP_INV(INV_ACCUM, true) else PP_INV(INV_ACCUM, false)
+  } else {
+    if (accumulate) PP_INV(INV_STORE, true) else PP_INV(INV_STORE, false)
+  }
+#undef PP_INV
   return cudaGetLastError();
 }
 
@@ -318,11 +369,11 @@ template cudaError_t launch_fwd_x<float, float>(const Geometry&, const DevTables
 template cudaError_t launch_fwd_x<float, double>(const Geometry&, const DevTables&, const FftFactors&, FwdMode,
                                                  const FwdArgs&, cplx<float>*, cudaStream_t);
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                  const cplx<double>*, double*, double, cudaStream_t);
+                                                  const cplx<double>*, double*, double, bool, cudaStream_t);
 template cudaError_t launch_inv_x<float, float>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                const cplx<float>*, float*, double, cudaStream_t);
+                                                const cplx<float>*, float*, double, bool, cudaStream_t);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                 const cplx<float>*, double*, double, cudaStream_t);
+                                                 const cplx<float>*, double*, double, bool, cudaStream_t);
 template cudaError_t launch_fft_z<double>(const Geometry&, const DevTables&, const FftFactors&, int, cplx<double>*,
                                           cudaStream_t);
 template cudaError_t launch_fft_z<float>(const Geometry&, const DevTables&, const FftFactors&, int, cplx<float>*,

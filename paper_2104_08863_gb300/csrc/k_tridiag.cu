@@ -214,7 +214,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 template <typename TD>
 __global__ void __launch_bounds__(32) k_mode00(Geometry g, const double* __restrict__ dy,
-                                               const double* __restrict__ h, cplx<TD>* __restrict__ spec) {
+                                               const double* __restrict__ h, cplx<TD>* __restrict__ spec,
+                                               double* __restrict__ acc, int gauge) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* fr = reinterpret_cast<double*>(smem_raw);
   double* fi = fr + g.ny;
@@ -234,6 +235,8 @@ __global__ void __launch_bounds__(32) k_mode00(Geometry g, const double* __restr
   }
   sr = warp_sum(sr); si = warp_sum(si); sw = warp_sum(sw);
   const double mr = sr / sw, mi = si / sw;
+  // <f> = (sum_j dy_j F_j) / (sum_j dy_j Nx Nz): kept for the residual of the refined solve
+  if (gauge == GAUGE_STORE_MEAN && lane == 0) acc[0] = mr / ((double)g.nx * (double)g.nz);
   // flux prefix sums, in place: q_j (inclusive)
   double lr = 0, li = 0;
   for (int j = lo; j < hi; ++j) {
@@ -269,6 +272,9 @@ __global__ void __launch_bounds__(32) k_mode00(Geometry g, const double* __restr
   }
   mr2 = warp_sum(mr2) / sw;
   mi2 = warp_sum(mi2) / sw;
+  // Offset gauge: the running total p has weighted sum acc[1]; shift this (0,0) profile by
+  // -acc[1] / sum(dy) so that sum_j dy_j (P_j + shift) = -acc[1].
+  if (gauge == GAUGE_OFFSET) mr2 += acc[1] / sw;
   for (int j = lo; j < hi; ++j)
     st_c(spec + (size_t)j * rstride, mk<TD>(TD(fr[j] - mr2), TD(fi[j] - mi2)));
 }
@@ -334,15 +340,16 @@ cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int par
 }
 
 template <typename TD>
-cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, bool, cplx<TD>* spec, cudaStream_t st) {
+cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, GaugeMode gauge, cplx<TD>* spec, cudaStream_t st) {
   const size_t smem = 2 * (size_t)g.ny * sizeof(double);
   auto kern = k_mode00<TD>;
   cudaError_t e;
   if ((e = prep(kern, smem)) != cudaSuccess) return e;
-  kern<<<1, 32, smem, st>>>(g, tb.dy, tb.h, spec);
+  kern<<<1, 32, smem, st>>>(g, tb.dy, tb.h, spec, tb.acc, (int)gauge);
   return cudaGetLastError();
 }
-template cudaError_t launch_mode00<double>(const Geometry&, const DevTables&, bool, cplx<double>*, cudaStream_t);
-template cudaError_t launch_mode00<float>(const Geometry&, const DevTables&, bool, cplx<float>*, cudaStream_t);
+template cudaError_t launch_mode00<double>(const Geometry&, const DevTables&, GaugeMode, cplx<double>*,
+                                           cudaStream_t);
+template cudaError_t launch_mode00<float>(const Geometry&, const DevTables&, GaugeMode, cplx<float>*, cudaStream_t);
 
 }  // namespace pp
