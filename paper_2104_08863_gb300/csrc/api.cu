@@ -81,8 +81,27 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
   dt.lamz = (const double*)(tb + to[11]);
   dt.dy = (const double*)(tb + to[12]);
   dt.h = (const double*)(tb + to[13]);
+  dt.d.inv_dy = (const double*)(tb + to[14]);
+  dt.d.inv_h = (const double*)(tb + to[15]);
+  dt.f.inv_dy = (const float*)(tb + to[16]);
+  dt.f.inv_h = (const float*)(tb + to[17]);
   dt.status = (int*)(base + pl->off_status);
   dt.acc = (double*)(base + pl->off_acc);
+  dt.tri = TriFactors{};
+  if (pl->off_tri) {
+    const size_t nsys = (size_t)pl->g.nz * pl->g.ncols;
+    const size_t rows = nsys * pl->g.ny, blks = nsys * pl->parts;
+    double* t = (double*)(base + pl->off_tri);
+    dt.tri.mult = t;
+    dt.tri.kappa = t + rows;
+    dt.tri.rb = t + 2 * rows;
+    dt.tri.gv = t + 3 * rows;
+    dt.tri.vF = t + 4 * rows;
+    dt.tri.vL = t + 4 * rows + blks;
+    dt.tri.wF = t + 4 * rows + 2 * blks;
+    dt.tri.wL = t + 4 * rows + 3 * blks;
+    dt.tri.nsys = (int)nsys;
+  }
   return dt;
 }
 }  // namespace pp
@@ -192,6 +211,8 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   slot(8, 4 * (size_t)ny);    slot(9, 4 * (size_t)ny);
   slot(10, 8 * (size_t)g.ncols); slot(11, 8 * (size_t)g.nz);
   slot(12, 8 * (size_t)ny);   slot(13, 8 * (size_t)(ny + 1));
+  slot(14, 8 * (size_t)ny);   slot(15, 8 * (size_t)(ny + 1));
+  slot(16, 4 * (size_t)ny);   slot(17, 4 * (size_t)(ny + 1));
   const size_t tab_bytes = off;
   pl->host_tables.assign(tab_bytes, 0);
   auto& img = pl->host_tables;
@@ -209,6 +230,13 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   put_real_table<double>(img, to[11], pl->lamz);
   put_real_table<double>(img, to[12], pl->dy);
   put_real_table<double>(img, to[13], pl->h);
+  std::vector<double> inv_dy(ny), inv_h(ny + 1, 0.0);
+  for (int j = 0; j < ny; ++j) inv_dy[j] = 1.0 / pl->dy[j];
+  for (int j = 1; j < ny; ++j) inv_h[j] = 1.0 / pl->h[j];
+  put_real_table<double>(img, to[14], inv_dy);
+  put_real_table<double>(img, to[15], inv_h);
+  put_real_table<float>(img, to[16], inv_dy);
+  put_real_table<float>(img, to[17], inv_h);
 
   // --- workspace layout ---
   const size_t csz = spec_is_fp64(pl) ? 16 : 8;
@@ -221,6 +249,12 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   pl->off_tables = off; off = align_up(off + tab_bytes, 256);
   pl->off_status = off; off = align_up(off + 256, 256);
   pl->off_acc = off;    off = align_up(off + 256, 256);
+  pl->off_tri = 0;
+  if (d->precision == PP_FP64) {   // per-mode PDD factors: 4 per row, 4 per block
+    const size_t nsys = (size_t)g.nz * g.ncols;
+    pl->off_tri = off;
+    off = align_up(off + 8 * nsys * (4 * (size_t)ny + 4 * (size_t)P), 256);
+  }
   pl->ws_bytes = off;
   pl->ws = nullptr;
   pl->launches = 0;
@@ -250,6 +284,10 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return PS_ECUDA;
   pl->ws = base;
   pl->dt = pp::bind_tables(pl, base);
+  if (pl->off_tri) {
+    if (launch_tridiag_setup(pl->g, pl->dt, pl->parts, st) != cudaSuccess) return PS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  }
   return PS_OK;
 }
 
@@ -311,7 +349,7 @@ poisson_status spectral_core<double>(Exec& ex, cplx<double>* spec, GaugeMode gau
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
   PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, ex.dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", (launch_tridiag<double, double>(g, ex.dt, pl->parts, -1, false, spec, st)));
+  PP_TRY_N("tridiag_pdd", launch_tridiag_factored(g, ex.dt, pl->parts, spec, st));
   PP_TRY_N("mode00", launch_mode00<double>(g, ex.dt, gauge, spec, st));
   PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, ex.dt, pl->fz, +1, spec, st));
   return PS_OK;

@@ -122,16 +122,16 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, FwdArgs args, Tables<
         z = mk<T>(T(a * s), T(b * s));
       } else if (MODE == FWD_DIV) {
         TI f0, f1;
-        const TI inv_dy = TI(1.0) / TI(tb.dy[j]);
+        const TI inv_dy = TI(tt.inv_dy[j]);
         divergence_pair<TI>(g, reinterpret_cast<const TI*>(args.u), reinterpret_cast<const TI*>(args.v),
                             reinterpret_cast<const TI*>(args.w), j, k, i0, inv_dx, inv_dy, inv_dz, f0, f1);
         const TI s = TI(args.in_scale);
         z = mk<T>(T(f0 * s), T(f1 * s));
       } else if (MODE == FWD_GRADT) {
         TI f0, f1;
-        const TI inv_hj = j >= 1 ? TI(1.0) / TI(tb.h[j]) : TI(0);
-        const TI inv_hj1 = j + 1 <= g.ny - 1 ? TI(1.0) / TI(tb.h[j + 1]) : TI(0);
-        const TI inv_dy = TI(1.0) / TI(tb.dy[j]);
+        const TI inv_hj = TI(tt.inv_h[j]);        // 0 on the walls
+        const TI inv_hj1 = TI(tt.inv_h[j + 1]);
+        const TI inv_dy = TI(tt.inv_dy[j]);
         gradT_pair<TI>(g, reinterpret_cast<const TI*>(args.u), reinterpret_cast<const TI*>(args.v),
                        reinterpret_cast<const TI*>(args.w), j, k, i0, inv_dx, inv_dz, inv_hj, inv_hj1, inv_dy, f0,
                        f1);

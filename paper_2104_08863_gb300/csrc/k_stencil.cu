@@ -14,10 +14,10 @@ namespace pp {
 template <typename T>
 __global__ void __launch_bounds__(256) k_gradient(Geometry g, const T* __restrict__ p, T* __restrict__ u,
                                                   T* __restrict__ v, T* __restrict__ w,
-                                                  const double* __restrict__ h, T dt) {
+                                                  const T* __restrict__ inv_h, T dt) {
   const size_t plane = (size_t)g.nz * g.nx;
   const size_t total = (size_t)(g.ny + 1) * plane;
-  const T cx = dt / T(g.dx), cz = dt / T(g.dz);
+  const T cx = T(dt / g.dx), cz = T(dt / g.dz);
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(idx / plane);
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_gradient(Geometry g, const T* __restric
       w[idx] -= cz * (pc - pzm);
     }
     if (j >= 1 && j <= g.ny - 1) {
-      const T cy = dt / T(h[j]);
+      const T cy = dt * inv_h[j];
       v[idx] -= cy * (p[idx] - p[idx - plane]);
     }
   }
@@ -81,11 +81,15 @@ static int stream_grid(size_t total) {
   return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
 }
 
+template <typename T> static const T* inv_h_table(const DevTables& tb);
+template <> const double* inv_h_table<double>(const DevTables& tb) { return tb.d.inv_h; }
+template <> const float* inv_h_table<float>(const DevTables& tb) { return tb.f.inv_h; }
+
 template <typename T>
 cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
                             cudaStream_t st) {
   const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
-  k_gradient<T><<<stream_grid(total), 256, 0, st>>>(g, p, u, v, w, tb.h, T(dt));
+  k_gradient<T><<<stream_grid(total), 256, 0, st>>>(g, p, u, v, w, inv_h_table<T>(tb), T(dt));
   return cudaGetLastError();
 }
 

@@ -192,6 +192,153 @@ __global__ void __launch_bounds__(512) k_tridiag(Geometry g, TriParams tp, const
   }
 }
 
+// ---- FP64 PDD with per-mode factors --------------------------------------------------------
+// On GB300 an FP64 division costs about ten FP64 instructions and FP64 issue is the bottleneck
+// of the FP64 path, so the RHS-independent part of each block's elimination (pivots, spikes
+// and the first-row weights kappa) is computed once per plan.  Per solve a thread then does,
+// for its m rows: g_j = -F_j + mult_j g_{j-1}, x~_{r0} += kappa_j g_j (forward, 4 FP64 ops),
+// the exact reduced system, and x_j = (g_j + alpha gv_j + c_j x_{j+1}) rb_j (backward, 6 ops).
+
+__device__ __forceinline__ void sys_to_mode(int sys, int ncols, int& kx, int& kz) {
+  kz = sys / ncols;
+  kx = sys - kz * ncols;
+}
+
+__global__ void __launch_bounds__(256) k_tridiag_setup(Geometry g, int P, int m, const double* __restrict__ a,
+                                                       const double* __restrict__ c,
+                                                       const double* __restrict__ lamx,
+                                                       const double* __restrict__ lamz, TriFactors tf) {
+  const int nsys = tf.nsys;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)nsys * P) return;
+  const int b = (int)(tid / nsys), sys = (int)(tid - (long long)b * nsys);
+  int kx, kz;
+  sys_to_mode(sys, g.ncols, kx, kz);
+  // (0,0) is solved elsewhere; give it a harmless positive shift so its factors stay finite
+  const double sigma = (kx == 0 && kz == 0) ? 1.0 : -(lamx[kx] + lamz[kz]);
+  const int r0 = b * m, r1 = r0 + m - 1;
+  double e = a[r0] + sigma, gvv = a[r0], rbp = 0.0, run = 1.0, vF = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const int j = r0 + i;
+    double mult = 0.0;
+    if (i > 0) {
+      mult = a[j] * rbp;
+      e = sigma + mult * e;
+      gvv = mult * gvv;
+    }
+    const double rb = 1.0 / (c[j] + e);
+    const double kappa = run * rb;
+    const size_t o = (size_t)j * nsys + sys;
+    tf.mult[o] = mult;
+    tf.rb[o] = rb;
+    tf.gv[o] = gvv;
+    tf.kappa[o] = kappa;
+    vF += kappa * gvv;
+    run *= c[j] * rb;
+    rbp = rb;
+  }
+  const size_t ob = (size_t)b * nsys + sys;
+  tf.vF[ob] = vF;
+  tf.vL[ob] = gvv * rbp;
+  tf.wF[ob] = tf.kappa[(size_t)r1 * nsys + sys] * c[r1];
+  tf.wL[ob] = c[r1] * rbp;
+}
+
+__global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int m, int S,
+                                                          const double* __restrict__ c, TriFactors tf,
+                                                          cplx<double>* __restrict__ spec) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const int PS = P * S;
+  double* xFr = sm;          double* xFi = sm + PS;      double* xLr = sm + 2 * PS;  double* xLi = sm + 3 * PS;
+  double* alr = sm + 4 * PS; double* ali = sm + 5 * PS;  double* ber = sm + 6 * PS;  double* bei = sm + 7 * PS;
+  double* y0r = sm + 8 * PS; double* y0i = sm + 9 * PS;  double* y1r = sm + 10 * PS; double* y1i = sm + 11 * PS;
+  double* X01s = sm + 12 * PS; double* X11s = sm + 13 * PS;
+  const int nsys = tf.nsys;
+  const int tid = threadIdx.x;
+  const int b = tid / S, s = tid - b * S;
+  const int sys = blockIdx.x * S + s;
+  int kx = 0, kz = 0;
+  bool active = sys < nsys;
+  if (active) {
+    sys_to_mode(sys, g.ncols, kx, kz);
+    if (kx == 0 && kz == 0) active = false;
+  }
+  const size_t rstride = (size_t)g.nz * g.pitch;
+  cplx<double>* col = spec + (size_t)kz * g.pitch + kx;
+  const int r0 = b * m;
+  const int me = b * S + s;
+  // ---- forward elimination and the block's end values of x~ ----
+  cplx<double> xF = mk(0.0, 0.0), xL = mk(0.0, 0.0);
+  if (active) {
+    cplx<double> gg = mk(0.0, 0.0);
+    for (int i = 0; i < m; ++i) {
+      const int j = r0 + i;
+      const size_t o = (size_t)j * nsys + sys;
+      const cplx<double> F = ld_c(col + (size_t)j * rstride);
+      const double mult = tf.mult[o], kap = tf.kappa[o];
+      gg = mk(fma(mult, gg.x, -F.x), fma(mult, gg.y, -F.y));
+      xF = mk(fma(kap, gg.x, xF.x), fma(kap, gg.y, xF.y));
+      st_c(col + (size_t)j * rstride, gg);
+    }
+    const double rbl = tf.rb[(size_t)(r0 + m - 1) * nsys + sys];
+    xL = mk(gg.x * rbl, gg.y * rbl);
+  }
+  cplx<double> alpha = mk(0.0, 0.0), beta = mk(0.0, 0.0);
+  if (P > 1) {
+    xFr[me] = xF.x; xFi[me] = xF.y; xLr[me] = xL.x; xLi[me] = xL.y;
+    __syncthreads();
+    if (b == 0 && active) {
+      // exact reduced system over the interfaces, unknowns z_i = (L_i, F_{i+1})
+      double pX01 = 0.0;
+      cplx<double> py0 = mk(0.0, 0.0);
+      for (int i = 0; i < P - 1; ++i) {
+        const int ii = i * S + s, in = (i + 1) * S + s;
+        const size_t bi = (size_t)i * nsys + sys, bn = (size_t)(i + 1) * nsys + sys;
+        const double vLi = tf.vL[bi], wLi = tf.wL[bi], vFn = tf.vF[bn], wFi = tf.wF[bi];
+        const double d01 = -wLi - vLi * wFi * pX01, d10 = -vFn;
+        const double inv = 1.0 / (1.0 - d01 * d10);
+        const double X00 = inv, X01 = -d01 * inv, X10 = -d10 * inv, X11 = inv;
+        const cplx<double> q0 = mk(xLr[ii] + vLi * py0.x, xLi[ii] + vLi * py0.y);
+        const cplx<double> q1 = mk(xFr[in], xFi[in]);
+        const cplx<double> y0 = mk(X00 * q0.x + X01 * q1.x, X00 * q0.y + X01 * q1.y);
+        const cplx<double> y1 = mk(X10 * q0.x + X11 * q1.x, X10 * q0.y + X11 * q1.y);
+        y0r[ii] = y0.x; y0i[ii] = y0.y; y1r[ii] = y1.x; y1i[ii] = y1.y;
+        X01s[ii] = X01; X11s[ii] = X11;
+        pX01 = X01;
+        py0 = y0;
+      }
+      cplx<double> z1n = mk(0.0, 0.0);
+      for (int i = P - 2; i >= 0; --i) {
+        const int ii = i * S + s;
+        const double t = (i == P - 2) ? 0.0 : tf.wF[(size_t)(i + 1) * nsys + sys];
+        const cplx<double> z0 = mk(y0r[ii] + t * z1n.x * X01s[ii], y0i[ii] + t * z1n.y * X01s[ii]);
+        const cplx<double> z1 = mk(y1r[ii] + t * z1n.x * X11s[ii], y1i[ii] + t * z1n.y * X11s[ii]);
+        alr[(i + 1) * S + s] = z0.x; ali[(i + 1) * S + s] = z0.y;
+        ber[ii] = z1.x; bei[ii] = z1.y;
+        z1n = z1;
+      }
+    }
+    __syncthreads();
+    if (b > 0) alpha = mk(alr[me], ali[me]);
+    if (b < P - 1) beta = mk(ber[me], bei[me]);
+  }
+  // ---- backward sweep with the neighbour values folded in ----
+  if (active) {
+    cplx<double> xn = beta;
+    for (int i = m - 1; i >= 0; --i) {
+      const int j = r0 + i;
+      const size_t o = (size_t)j * nsys + sys;
+      const double rb = tf.rb[o], gv = tf.gv[o], cj = c[j];
+      const cplx<double> gj = ld_c(col + (size_t)j * rstride);
+      const double tx = fma(cj, xn.x, fma(alpha.x, gv, gj.x));
+      const double ty = fma(cj, xn.y, fma(alpha.y, gv, gj.y));
+      xn = mk(tx * rb, ty * rb);
+      st_c(col + (size_t)j * rstride, xn);
+    }
+  }
+}
+
 // The (0, 0) mode: T p = F - mean with sum_j dy_j p_j = 0 (compatibility and gauge), by the
 // exact flux prefix sums  q_j = sum_{l<=j} dy_l F^c_l,  p_0 = 0,  p_{j+1} = p_j + h_{j+1} q_j,
 // followed by removal of the dy-weighted mean.  One warp, FP64, chunked warp scans.
@@ -337,6 +484,27 @@ cudaError_t launch_tridiag<float, float>(const Geometry& g, const DevTables& tb,
 cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                  cplx<float>* spec, cplx<double>* scratch, cudaStream_t st) {
   return launch_tridiag_impl<float, double, true>(g, tb, parts, low_modes, true, spec, scratch, st);
+}
+
+cudaError_t launch_tridiag_setup(const Geometry& g, const DevTables& tb, int parts, cudaStream_t st) {
+  const long long n = (long long)tb.tri.nsys * parts;
+  const int blocks = (int)((n + 255) / 256);
+  k_tridiag_setup<<<blocks, 256, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c, tb.lamx, tb.lamz, tb.tri);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, cplx<double>* spec,
+                                    cudaStream_t st) {
+  int S = 256 / parts;
+  if (S < 1) S = 1;
+  if (S > 32) S = 32;
+  const size_t smem = (size_t)14 * parts * S * sizeof(double);
+  const int blocks = (tb.tri.nsys + S - 1) / S;
+  auto kern = k_tridiag_factored;
+  cudaError_t e;
+  if ((e = prep(kern, smem)) != cudaSuccess) return e;
+  kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, tb.d.c, tb.tri, spec);
+  return cudaGetLastError();
 }
 
 template <typename TD>

@@ -46,11 +46,13 @@ extern "C" poisson_status poisson_solve_static_ws(poisson_plan_t pl, const void*
   poisson_status s = static_workspace_address(&ws);
   if (s != PS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  // The array keeps whatever the previous call left: reload this plan's tables and clear the
-  // status word (the only region that must start at zero) on every call.
+  // The array keeps whatever the previous call left: reload this plan's tables, rebuild its
+  // FP64 PDD factors and clear the status word (the only region that must start at zero).
   if (cudaMemcpyAsync(ws + pl->off_tables, pl->host_tables.data(), pl->host_tables.size(),
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
     return PS_ECUDA;
   if (cudaMemsetAsync(ws + pl->off_status, 0, 256, st) != cudaSuccess) return PS_ECUDA;
-  return pp::solve_on_workspace(pl, ws, pp::bind_tables(pl, ws), rhs, p, st);
+  const pp::DevTables dt = pp::bind_tables(pl, ws);
+  if (pl->off_tri && pp::launch_tridiag_setup(pl->g, dt, pl->parts, st) != cudaSuccess) return PS_ECUDA;
+  return pp::solve_on_workspace(pl, ws, dt, rhs, p, st);
 }
