@@ -289,6 +289,7 @@ def run_gpu(args):
     h2d = 8 * (3 * CASE.npoints + CASE.nx * CASE.nz)
     d2h = h2d + 8 * CASE.npoints
 
+    forms = precision_forms(dev) if (world == 1 and not args.no_forms) else None
     cpu = oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -298,10 +299,61 @@ def run_gpu(args):
                "cpu_baseline": cpu,
                "e2e": {"value": world * CASE.npoints / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-               "gpu_launches": launches_per_step * args.steps, "clocks": clk}
+               "gpu_launches": launches_per_step * args.steps, "clocks": clk, "precision_forms": forms}
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def precision_forms(dev, steps: int = 5, warmup: int = 3):
+    """FP64 plain vs FP32 vs FP32-refined Poisson solves on the 1536 x 768 x 1024 channel.
+
+    Right-hand side: seeded N(0, 1) field (torch generator seed 2) on the device.  Each form
+    is timed with CUDA events over `steps` solves; its result is compared with the plain
+    FP64 solve's (max |difference| / max |p|), which matches the oracle to 1e-12 in the
+    parity tests.  Returns a dict for the JSON line.
+    """
+    import torch
+    import paper_2104_08863_gb300 as P
+    case = W.CHANNEL_1536
+    faces = W.tanh_faces(case.ny, case.stretch)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    f = torch.randn(case.ny, case.nz, case.nx, dtype=torch.float64, device=dev, generator=gen)
+    out = {"workload": f"{case.name} Poisson solve, N(0,1) rhs (seed 2)", "grid": [case.nx, case.ny, case.nz]}
+    ref = None
+    forms = [("fp64", P.PP_FP64, 0), ("fp32", P.PP_FP32, 0), ("fp32_refined_1", P.PP_FP32_REFINED, 1),
+             ("fp32_refined_2", P.PP_FP32_REFINED, 2)]
+    for name, prec, steps_r in forms:
+        plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, fp64_low_modes=4,
+                      refine_steps=max(steps_r, 1), flags=P.POISSON_TIMING, device=dev)
+        rhs = f.float() if prec == P.PP_FP32 else f
+        p = torch.empty_like(rhs)
+        for _ in range(warmup):
+            plan.solve(rhs, out=p)
+        stream = torch.cuda.current_stream(dev)
+        stage = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve(rhs, out=p)
+            for k, ms in plan.stage_times():
+                stage[k] = stage.get(k, 0.0) + ms
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        entry = {"ms": ms, "gpts_s": case.npoints / (ms * 1e-3) / 1e9,
+                 "stage_ms": {k: round(v / steps, 4) for k, v in sorted(stage.items(), key=lambda kv: -kv[1])}}
+        if ref is None:
+            ref = p.clone()
+            scale = float(ref.abs().max())
+        else:
+            entry["maxrel_vs_fp64"] = float((p.double() - ref).abs().max()) / scale
+        out[name] = entry
+        del plan, p
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -311,11 +363,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 1536x768x1024 precision-form comparison")
+    ap.add_argument("--forms-only", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.forms_only:
+        import torch
+        from paper_2104_08863_gb300 import build as b
+        b.build()
+        print(json.dumps(precision_forms(torch.device("cuda", 0))))
     else:
         run_gpu(args)
 

@@ -79,6 +79,11 @@ template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
                          cudaStream_t st);
 
+// Specialised z-transform for Nz in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+// returns cudaErrorNotSupported for other lengths.
+template <typename T>
+cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st);
+
 template <typename TD, typename TC>
 cudaError_t launch_tridiag(const Geometry& g, const DevTables& tb, int parts, int low_modes, bool low_list,
                            cplx<TD>* spec, cudaStream_t st);

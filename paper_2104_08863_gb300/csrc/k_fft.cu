@@ -344,6 +344,10 @@ cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactor
 template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
                          cudaStream_t st) {
+  {
+    const cudaError_t ef = launch_fft_z_fast<T>(g, tabs<T>(tb), sign, spec, st);
+    if (ef != cudaErrorNotSupported) return ef;
+  }
   int W = (int)(64 / sizeof(cplx<T>));           // 64-byte row segments
   while (W * fz.L < 2048 && W < 32) W *= 2;       // small Nz: widen the tile
   if (W > g.ncols) W = g.ncols;

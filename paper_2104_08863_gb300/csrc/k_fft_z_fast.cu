@@ -1,0 +1,90 @@
+// Specialised z-transform kernel (step (4) / (6) of Sec. 3.1): a CTA transforms a tile of W
+// adjacent kx columns of one y-plane along z (Nz points each).  The tile is loaded with
+// coalesced row segments of W complex values, transformed in place in (padded) shared memory
+// by the compile-time Stockham engine, and stored back.  W and the thread count are chosen so
+// that each thread stages 16 (FP32) or 8 (FP64) complex values per stage, which keeps two
+// CTAs resident per SM so that one CTA's loads overlap the other's arithmetic.
+#include "fft_static.cuh"
+#include "internal.h"
+
+namespace pp {
+
+template <typename T, int NZ> struct ZTile {
+  static constexpr int E = sizeof(T) == 4 ? 16 : 8;               // complex values per thread
+  static constexpr int WMIN = sizeof(T) == 4 ? 8 : 4;             // 64-byte row segments
+  static constexpr int W0 = (E * 512) / NZ;
+  static constexpr int W = W0 < WMIN ? WMIN : (W0 > 32 ? 32 : W0);
+  static constexpr int T0 = W * NZ / E;
+  static constexpr int THREADS = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
+  static constexpr int SMEM = padded_size<T>(W * NZ) * (int)sizeof(cplx<T>);
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;   // FP32: two CTAs per SM (<= 64 registers)
+};
+
+template <typename T, int NZ, int SIGN>
+__global__ void __launch_bounds__(ZTile<T, NZ>::THREADS, ZTile<T, NZ>::MINB) k_fft_z_fast(Geometry g, Tables<T> tt,
+                                                                       cplx<T>* __restrict__ spec) {
+  using C = ZTile<T, NZ>;
+  constexpr int W = C::W, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int j = blockIdx.y;
+  const int kx0 = blockIdx.x * W;
+  cplx<T>* plane = spec + (size_t)j * NZ * g.pitch + kx0;
+  const int ncol = min(W, g.ncols - kx0);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < NZ * W; idx += THREADS) {
+    const int n = idx / W, c = idx % W;
+    buf[padi<T>(idx)] = c < ncol ? ld_c(plane + (size_t)n * g.pitch + c) : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  fft_static<T, NZ, SIGN, W, THREADS, W, 1, true>(buf, tt.tw_z);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < NZ * W; idx += THREADS) {
+    const int n = idx / W, c = idx % W;
+    if (c < ncol) st_c(plane + (size_t)n * g.pitch + c, buf[padi<T>(idx)]);
+  }
+}
+
+template <typename T, int NZ>
+static cudaError_t launch_z(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st) {
+  using C = ZTile<T, NZ>;
+  const dim3 grid((g.ncols + C::W - 1) / C::W, g.ny);
+  cudaError_t e;
+  if (sign < 0) {
+    auto k = k_fft_z_fast<T, NZ, -1>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
+  } else {
+    auto k = k_fft_z_fast<T, NZ, 1>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
+  }
+  return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported when Nz has no specialisation (the caller then uses the
+// generic kernel).
+template <typename T>
+cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st) {
+  switch (g.nz) {
+    case 16: return launch_z<T, 16>(g, tt, sign, spec, st);
+    case 32: return launch_z<T, 32>(g, tt, sign, spec, st);
+    case 48: return launch_z<T, 48>(g, tt, sign, spec, st);
+    case 64: return launch_z<T, 64>(g, tt, sign, spec, st);
+    case 96: return launch_z<T, 96>(g, tt, sign, spec, st);
+    case 128: return launch_z<T, 128>(g, tt, sign, spec, st);
+    case 192: return launch_z<T, 192>(g, tt, sign, spec, st);
+    case 256: return launch_z<T, 256>(g, tt, sign, spec, st);
+    case 384: return launch_z<T, 384>(g, tt, sign, spec, st);
+    case 512: return launch_z<T, 512>(g, tt, sign, spec, st);
+    case 768: return launch_z<T, 768>(g, tt, sign, spec, st);
+    case 1024: return launch_z<T, 1024>(g, tt, sign, spec, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template cudaError_t launch_fft_z_fast<float>(const Geometry&, const Tables<float>&, int, cplx<float>*, cudaStream_t);
+template cudaError_t launch_fft_z_fast<double>(const Geometry&, const Tables<double>&, int, cplx<double>*,
+                                               cudaStream_t);
+
+}  // namespace pp
