@@ -87,20 +87,24 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
   dt.f.inv_h = (const float*)(tb + to[17]);
   dt.status = (int*)(base + pl->off_status);
   dt.acc = (double*)(base + pl->off_acc);
-  dt.tri = TriFactors{};
-  if (pl->off_tri) {
+  dt.tri_d = TriFactors<double>{};
+  dt.tri_f = TriFactors<float>{};
+  {
     const size_t nsys = (size_t)pl->g.nz * pl->g.ncols;
     const size_t rows = nsys * pl->g.ny, blks = nsys * pl->parts;
-    double* t = (double*)(base + pl->off_tri);
-    dt.tri.mult = t;
-    dt.tri.kappa = t + rows;
-    dt.tri.rb = t + 2 * rows;
-    dt.tri.gv = t + 3 * rows;
-    dt.tri.vF = t + 4 * rows;
-    dt.tri.vL = t + 4 * rows + blks;
-    dt.tri.wF = t + 4 * rows + 2 * blks;
-    dt.tri.wL = t + 4 * rows + 3 * blks;
-    dt.tri.nsys = (int)nsys;
+    if (pl->precision == PP_FP64) {
+      double* t = (double*)(base + pl->off_tri);
+      TriFactors<double>& f = dt.tri_d;
+      f.mult = t; f.kappa = t + rows; f.rb = t + 2 * rows; f.gv = t + 3 * rows;
+      f.vF = t + 4 * rows; f.vL = f.vF + blks; f.wF = f.vL + blks; f.wL = f.wF + blks;
+      f.nsys = (int)nsys;
+    } else {
+      float* t = (float*)(base + pl->off_tri);
+      TriFactors<float>& f = dt.tri_f;
+      f.mult = nullptr; f.kappa = nullptr; f.rb = t; f.gv = t + rows;
+      f.vF = t + 2 * rows; f.vL = f.vF + blks; f.wF = f.vL + blks; f.wL = f.wF + blks;
+      f.nsys = (int)nsys;
+    }
   }
   return dt;
 }
@@ -249,11 +253,11 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   pl->off_tables = off; off = align_up(off + tab_bytes, 256);
   pl->off_status = off; off = align_up(off + 256, 256);
   pl->off_acc = off;    off = align_up(off + 256, 256);
-  pl->off_tri = 0;
-  if (d->precision == PP_FP64) {   // per-mode PDD factors: 4 per row, 4 per block
+  {   // per-mode PDD factors: FP64 plans 4 per row + 4 per block; FP32 plans 2 per row + 4 per block
     const size_t nsys = (size_t)g.nz * g.ncols;
     pl->off_tri = off;
-    off = align_up(off + 8 * nsys * (4 * (size_t)ny + 4 * (size_t)P), 256);
+    if (d->precision == PP_FP64) off = align_up(off + 8 * nsys * (4 * (size_t)ny + 4 * (size_t)P), 256);
+    else off = align_up(off + 4 * nsys * (2 * (size_t)ny + 4 * (size_t)P), 256);
   }
   pl->ws_bytes = off;
   pl->ws = nullptr;
@@ -361,7 +365,7 @@ poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
   PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", (launch_tridiag<float, float>(g, ex.dt, pl->parts, pl->low, false, spec, st)));
+  PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, spec, st));
   if (pl->low >= 0) {
     cplx<double>* scr = (cplx<double>*)(ex.ws + pl->off_scratch);
     PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, st));

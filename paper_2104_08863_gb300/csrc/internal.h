@@ -21,15 +21,16 @@ template <typename T> struct Tables {
   const T* inv_h;          // 1 / h_j for interior faces j = 1..ny-1, 0 on the walls
 };
 
-// Per-mode PDD factors of the FP64 path, built once by k_tridiag_setup (layout [row][system]
+// Per-mode PDD factors, built once by k_tridiag_setup (layout [row][system]
 // and [block][system], system = kz * (Nx/2+1) + kx).  For block rows r0..r1 of one system:
 //   mult_j = a_j / beta_{j-1} (0 at r0), rb_j = 1 / beta_j, gv_j = forward-eliminated spike
 //   a_{r0} e_1, kappa_j = rb_j prod_{r0<=l<j} c_l rb_l (so x~_{r0} = sum_j kappa_j g_j);
 //   vF, vL, wF, wL = first/last-row values of the spikes v = A_i^-1 a e_1, w = A_i^-1 c e_m.
-struct TriFactors {
-  double *mult, *kappa, *rb, *gv;
-  double *vF, *vL, *wF, *wL;
-  int nsys;
+// FP32 plans keep only rb and gv per row (mult and kappa are recomputed in the sweep).
+template <typename T> struct TriFactors {
+  T *mult, *kappa, *rb, *gv;
+  T *vF, *vL, *wF, *wL;
+  int nsys;   // 0 when the plan has no factors of this precision
 };
 
 struct DevTables {
@@ -41,7 +42,8 @@ struct DevTables {
   const double* h;         // centre distances across face j (j = 1..ny-1; h[0], h[ny] = 0)
   int* status;             // device status word
   double* acc;             // accumulators of the refined solve: [0] <f>, [1] sum_jki dy_j p_jki
-  TriFactors tri;          // FP64 plans only (null pointers otherwise)
+  TriFactors<double> tri_d;  // FP64 plans
+  TriFactors<float> tri_f;   // FP32 and FP32-refined plans
 };
 
 struct Geometry {
@@ -95,10 +97,12 @@ template <>
 cudaError_t launch_tridiag<float, float>(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                          bool low_list, cplx<float>* spec, cudaStream_t st);
 
-// FP64 PDD with the precomputed factors in tb.tri (setup once, then per solve).
+// PDD with the precomputed factors tb.tri_d / tb.tri_f (setup once per plan, then per solve).
 cudaError_t launch_tridiag_setup(const Geometry& g, const DevTables& tb, int parts, cudaStream_t st);
 cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, cplx<double>* spec,
                                     cudaStream_t st);
+cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                        cplx<float>* spec, cudaStream_t st);
 
 // FP64 re-solve of the low-mode list on FP32 spectral data (intermediates in FP64 scratch).
 cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,

@@ -192,22 +192,28 @@ __global__ void __launch_bounds__(512) k_tridiag(Geometry g, TriParams tp, const
   }
 }
 
-// ---- FP64 PDD with per-mode factors --------------------------------------------------------
-// On GB300 an FP64 division costs about ten FP64 instructions and FP64 issue is the bottleneck
-// of the FP64 path, so the RHS-independent part of each block's elimination (pivots, spikes
-// and the first-row weights kappa) is computed once per plan.  Per solve a thread then does,
-// for its m rows: g_j = -F_j + mult_j g_{j-1}, x~_{r0} += kappa_j g_j (forward, 4 FP64 ops),
-// the exact reduced system, and x_j = (g_j + alpha gv_j + c_j x_{j+1}) rb_j (backward, 6 ops).
+// ---- PDD with per-mode factors (the production path) ----------------------------------------
+// The RHS-independent part of each block's elimination (pivots, spikes, first-row weights)
+// depends only on the mode, so k_tridiag_setup computes it once per plan in FP64 and stores it
+// in the solve's precision.  Per solve a thread then runs, for its m rows,
+//   forward : g_j = -F_j + mult_j g_{j-1},  x~_{r0} += kappa_j g_j
+//   exact reduced interface system (Eq. 21, framed entries included)
+//   backward: x_j = (g_j + alpha gv_j + c_j x_{j+1}) rb_j
+// FULL (FP64, FP64-issue bound) reads mult and kappa from tables; the lean FP32 variant
+// (HBM bound) stores only rb and gv and recomputes mult_j = a_j rb_{j-1} and
+// kappa_j = rb_j prod c_l rb_l with a few FP32 multiplies.  Rows are processed in chunks of
+// CH so that a thread keeps CH independent loads in flight.
 
 __device__ __forceinline__ void sys_to_mode(int sys, int ncols, int& kx, int& kz) {
   kz = sys / ncols;
   kx = sys - kz * ncols;
 }
 
+template <typename T, bool FULL>
 __global__ void __launch_bounds__(256) k_tridiag_setup(Geometry g, int P, int m, const double* __restrict__ a,
                                                        const double* __restrict__ c,
                                                        const double* __restrict__ lamx,
-                                                       const double* __restrict__ lamz, TriFactors tf) {
+                                                       const double* __restrict__ lamz, TriFactors<T> tf) {
   const int nsys = tf.nsys;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)nsys * P) return;
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(256) k_tridiag_setup(Geometry g, int P, int m,
   // (0,0) is solved elsewhere; give it a harmless positive shift so its factors stay finite
   const double sigma = (kx == 0 && kz == 0) ? 1.0 : -(lamx[kx] + lamz[kz]);
   const int r0 = b * m, r1 = r0 + m - 1;
-  double e = a[r0] + sigma, gvv = a[r0], rbp = 0.0, run = 1.0, vF = 0.0;
+  double e = a[r0] + sigma, gvv = a[r0], rbp = 0.0, run = 1.0, vF = 0.0, kap = 0.0;
   for (int i = 0; i < m; ++i) {
     const int j = r0 + i;
     double mult = 0.0;
@@ -227,33 +233,37 @@ __global__ void __launch_bounds__(256) k_tridiag_setup(Geometry g, int P, int m,
       gvv = mult * gvv;
     }
     const double rb = 1.0 / (c[j] + e);
-    const double kappa = run * rb;
+    kap = run * rb;
     const size_t o = (size_t)j * nsys + sys;
-    tf.mult[o] = mult;
-    tf.rb[o] = rb;
-    tf.gv[o] = gvv;
-    tf.kappa[o] = kappa;
-    vF += kappa * gvv;
+    if constexpr (FULL) {
+      tf.mult[o] = T(mult);
+      tf.kappa[o] = T(kap);
+    }
+    tf.rb[o] = T(rb);
+    tf.gv[o] = T(gvv);
+    vF += kap * gvv;
     run *= c[j] * rb;
     rbp = rb;
   }
   const size_t ob = (size_t)b * nsys + sys;
-  tf.vF[ob] = vF;
-  tf.vL[ob] = gvv * rbp;
-  tf.wF[ob] = tf.kappa[(size_t)r1 * nsys + sys] * c[r1];
-  tf.wL[ob] = c[r1] * rbp;
+  tf.vF[ob] = T(vF);
+  tf.vL[ob] = T(gvv * rbp);
+  tf.wF[ob] = T(kap * c[r1]);
+  tf.wL[ob] = T(c[r1] * rbp);
 }
 
-__global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int m, int S,
-                                                          const double* __restrict__ c, TriFactors tf,
-                                                          cplx<double>* __restrict__ spec) {
+template <typename T, bool FULL>
+__global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int m, int S, int low,
+                                                          const T* __restrict__ a, const T* __restrict__ c,
+                                                          TriFactors<T> tf, cplx<T>* __restrict__ spec) {
+  constexpr int CH = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sm = reinterpret_cast<double*>(smem_raw);
+  T* sm = reinterpret_cast<T*>(smem_raw);
   const int PS = P * S;
-  double* xFr = sm;          double* xFi = sm + PS;      double* xLr = sm + 2 * PS;  double* xLi = sm + 3 * PS;
-  double* alr = sm + 4 * PS; double* ali = sm + 5 * PS;  double* ber = sm + 6 * PS;  double* bei = sm + 7 * PS;
-  double* y0r = sm + 8 * PS; double* y0i = sm + 9 * PS;  double* y1r = sm + 10 * PS; double* y1i = sm + 11 * PS;
-  double* X01s = sm + 12 * PS; double* X11s = sm + 13 * PS;
+  T* xFr = sm;          T* xFi = sm + PS;      T* xLr = sm + 2 * PS;  T* xLi = sm + 3 * PS;
+  T* alr = sm + 4 * PS; T* ali = sm + 5 * PS;  T* ber = sm + 6 * PS;  T* bei = sm + 7 * PS;
+  T* y0r = sm + 8 * PS; T* y0i = sm + 9 * PS;  T* y1r = sm + 10 * PS; T* y1i = sm + 11 * PS;
+  T* X01s = sm + 12 * PS; T* X11s = sm + 13 * PS;
   const int nsys = tf.nsys;
   const int tid = threadIdx.x;
   const int b = tid / S, s = tid - b * S;
@@ -262,79 +272,136 @@ __global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int
   bool active = sys < nsys;
   if (active) {
     sys_to_mode(sys, g.ncols, kx, kz);
-    if (kx == 0 && kz == 0) active = false;
+    if ((kx == 0 && kz == 0) || is_low(kx, kz, g.nz, low)) active = false;
   }
   const size_t rstride = (size_t)g.nz * g.pitch;
-  cplx<double>* col = spec + (size_t)kz * g.pitch + kx;
+  cplx<T>* col = spec + (size_t)kz * g.pitch + kx;
   const int r0 = b * m;
   const int me = b * S + s;
   // ---- forward elimination and the block's end values of x~ ----
-  cplx<double> xF = mk(0.0, 0.0), xL = mk(0.0, 0.0);
+  cplx<T> xF = mk<T>(T(0), T(0)), xL = mk<T>(T(0), T(0));
   if (active) {
-    cplx<double> gg = mk(0.0, 0.0);
-    for (int i = 0; i < m; ++i) {
-      const int j = r0 + i;
-      const size_t o = (size_t)j * nsys + sys;
-      const cplx<double> F = ld_c(col + (size_t)j * rstride);
-      const double mult = tf.mult[o], kap = tf.kappa[o];
-      gg = mk(fma(mult, gg.x, -F.x), fma(mult, gg.y, -F.y));
-      xF = mk(fma(kap, gg.x, xF.x), fma(kap, gg.y, xF.y));
-      st_c(col + (size_t)j * rstride, gg);
+    cplx<T> gg = mk<T>(T(0), T(0));
+    T rbp = T(0), run = T(1);
+    for (int i0 = 0; i0 < m; i0 += CH) {
+      cplx<T> F[CH];
+      T t1[CH], t2[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        if (i0 + q < m) {
+          const int j = r0 + i0 + q;
+          const size_t o = (size_t)j * nsys + sys;
+          F[q] = ld_c(col + (size_t)j * rstride);
+          if constexpr (FULL) {
+            t1[q] = tf.mult[o];
+            t2[q] = tf.kappa[o];
+          } else {
+            t1[q] = tf.rb[o];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        if (i0 + q < m) {
+          const int j = r0 + i0 + q;
+          T mult, kap;
+          if constexpr (FULL) {
+            mult = t1[q];
+            kap = t2[q];
+          } else {
+            const T rb = t1[q];
+            mult = (i0 + q == 0) ? T(0) : a[j] * rbp;
+            kap = run * rb;
+            run *= c[j] * rb;
+            rbp = rb;
+          }
+          gg = mk<T>(fma(mult, gg.x, -F[q].x), fma(mult, gg.y, -F[q].y));
+          xF = mk<T>(fma(kap, gg.x, xF.x), fma(kap, gg.y, xF.y));
+          F[q] = gg;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (i0 + q < m) st_c(col + (size_t)(r0 + i0 + q) * rstride, F[q]);
     }
-    const double rbl = tf.rb[(size_t)(r0 + m - 1) * nsys + sys];
-    xL = mk(gg.x * rbl, gg.y * rbl);
+    T rbl;
+    if constexpr (FULL) rbl = tf.rb[(size_t)(r0 + m - 1) * nsys + sys];
+    else rbl = rbp;
+    xL = mk<T>(gg.x * rbl, gg.y * rbl);
   }
-  cplx<double> alpha = mk(0.0, 0.0), beta = mk(0.0, 0.0);
+  cplx<T> alpha = mk<T>(T(0), T(0)), beta = mk<T>(T(0), T(0));
   if (P > 1) {
     xFr[me] = xF.x; xFi[me] = xF.y; xLr[me] = xL.x; xLi[me] = xL.y;
     __syncthreads();
     if (b == 0 && active) {
       // exact reduced system over the interfaces, unknowns z_i = (L_i, F_{i+1})
-      double pX01 = 0.0;
-      cplx<double> py0 = mk(0.0, 0.0);
+      T pX01 = T(0);
+      cplx<T> py0 = mk<T>(T(0), T(0));
       for (int i = 0; i < P - 1; ++i) {
         const int ii = i * S + s, in = (i + 1) * S + s;
         const size_t bi = (size_t)i * nsys + sys, bn = (size_t)(i + 1) * nsys + sys;
-        const double vLi = tf.vL[bi], wLi = tf.wL[bi], vFn = tf.vF[bn], wFi = tf.wF[bi];
-        const double d01 = -wLi - vLi * wFi * pX01, d10 = -vFn;
-        const double inv = 1.0 / (1.0 - d01 * d10);
-        const double X00 = inv, X01 = -d01 * inv, X10 = -d10 * inv, X11 = inv;
-        const cplx<double> q0 = mk(xLr[ii] + vLi * py0.x, xLi[ii] + vLi * py0.y);
-        const cplx<double> q1 = mk(xFr[in], xFi[in]);
-        const cplx<double> y0 = mk(X00 * q0.x + X01 * q1.x, X00 * q0.y + X01 * q1.y);
-        const cplx<double> y1 = mk(X10 * q0.x + X11 * q1.x, X10 * q0.y + X11 * q1.y);
+        const T vLi = tf.vL[bi], wLi = tf.wL[bi], vFn = tf.vF[bn], wFi = tf.wF[bi];
+        // eliminating z_{i-1} fills entry (0,1): L_i reaches F_{i+1} through L_{i-1} and F_i
+        const T d01 = -wLi - vLi * wFi * pX01, d10 = -vFn;
+        const T inv = T(1) / (T(1) - d01 * d10);
+        const T X00 = inv, X01 = -d01 * inv, X10 = -d10 * inv, X11 = inv;
+        const cplx<T> q0 = mk<T>(xLr[ii] + vLi * py0.x, xLi[ii] + vLi * py0.y);
+        const cplx<T> q1 = mk<T>(xFr[in], xFi[in]);
+        const cplx<T> y0 = mk<T>(X00 * q0.x + X01 * q1.x, X00 * q0.y + X01 * q1.y);
+        const cplx<T> y1 = mk<T>(X10 * q0.x + X11 * q1.x, X10 * q0.y + X11 * q1.y);
         y0r[ii] = y0.x; y0i[ii] = y0.y; y1r[ii] = y1.x; y1i[ii] = y1.y;
         X01s[ii] = X01; X11s[ii] = X11;
         pX01 = X01;
         py0 = y0;
       }
-      cplx<double> z1n = mk(0.0, 0.0);
+      cplx<T> z1n = mk<T>(T(0), T(0));
       for (int i = P - 2; i >= 0; --i) {
         const int ii = i * S + s;
-        const double t = (i == P - 2) ? 0.0 : tf.wF[(size_t)(i + 1) * nsys + sys];
-        const cplx<double> z0 = mk(y0r[ii] + t * z1n.x * X01s[ii], y0i[ii] + t * z1n.y * X01s[ii]);
-        const cplx<double> z1 = mk(y1r[ii] + t * z1n.x * X11s[ii], y1i[ii] + t * z1n.y * X11s[ii]);
-        alr[(i + 1) * S + s] = z0.x; ali[(i + 1) * S + s] = z0.y;
-        ber[ii] = z1.x; bei[ii] = z1.y;
+        const T tw = (i == P - 2) ? T(0) : tf.wF[(size_t)(i + 1) * nsys + sys];
+        const cplx<T> z0 = mk<T>(y0r[ii] + tw * z1n.x * X01s[ii], y0i[ii] + tw * z1n.y * X01s[ii]);
+        const cplx<T> z1 = mk<T>(y1r[ii] + tw * z1n.x * X11s[ii], y1i[ii] + tw * z1n.y * X11s[ii]);
+        alr[(i + 1) * S + s] = z0.x; ali[(i + 1) * S + s] = z0.y;   // alpha of block i+1 = L_i
+        ber[ii] = z1.x; bei[ii] = z1.y;                              // beta of block i = F_{i+1}
         z1n = z1;
       }
     }
     __syncthreads();
-    if (b > 0) alpha = mk(alr[me], ali[me]);
-    if (b < P - 1) beta = mk(ber[me], bei[me]);
+    if (b > 0) alpha = mk<T>(alr[me], ali[me]);
+    if (b < P - 1) beta = mk<T>(ber[me], bei[me]);
   }
   // ---- backward sweep with the neighbour values folded in ----
   if (active) {
-    cplx<double> xn = beta;
-    for (int i = m - 1; i >= 0; --i) {
-      const int j = r0 + i;
-      const size_t o = (size_t)j * nsys + sys;
-      const double rb = tf.rb[o], gv = tf.gv[o], cj = c[j];
-      const cplx<double> gj = ld_c(col + (size_t)j * rstride);
-      const double tx = fma(cj, xn.x, fma(alpha.x, gv, gj.x));
-      const double ty = fma(cj, xn.y, fma(alpha.y, gv, gj.y));
-      xn = mk(tx * rb, ty * rb);
-      st_c(col + (size_t)j * rstride, xn);
+    cplx<T> xn = beta;
+    for (int i1 = m; i1 > 0; i1 -= CH) {
+      cplx<T> G[CH];
+      T rbv[CH], gvv[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int i = i1 - 1 - q;
+        if (i >= 0) {
+          const int j = r0 + i;
+          const size_t o = (size_t)j * nsys + sys;
+          G[q] = ld_c(col + (size_t)j * rstride);
+          rbv[q] = tf.rb[o];
+          gvv[q] = tf.gv[o];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int i = i1 - 1 - q;
+        if (i >= 0) {
+          const T cj = c[r0 + i];
+          const T tx = fma(cj, xn.x, fma(alpha.x, gvv[q], G[q].x));
+          const T ty = fma(cj, xn.y, fma(alpha.y, gvv[q], G[q].y));
+          xn = mk<T>(tx * rbv[q], ty * rbv[q]);
+          G[q] = xn;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int i = i1 - 1 - q;
+        if (i >= 0) st_c(col + (size_t)(r0 + i) * rstride, G[q]);
+      }
     }
   }
 }
@@ -487,24 +554,42 @@ cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int par
 }
 
 cudaError_t launch_tridiag_setup(const Geometry& g, const DevTables& tb, int parts, cudaStream_t st) {
-  const long long n = (long long)tb.tri.nsys * parts;
-  const int blocks = (int)((n + 255) / 256);
-  k_tridiag_setup<<<blocks, 256, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c, tb.lamx, tb.lamz, tb.tri);
+  if (tb.tri_d.nsys) {
+    const long long n = (long long)tb.tri_d.nsys * parts;
+    k_tridiag_setup<double, true><<<(int)((n + 255) / 256), 256, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c,
+                                                                          tb.lamx, tb.lamz, tb.tri_d);
+  }
+  if (tb.tri_f.nsys) {
+    const long long n = (long long)tb.tri_f.nsys * parts;
+    k_tridiag_setup<float, false><<<(int)((n + 255) / 256), 256, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c,
+                                                                          tb.lamx, tb.lamz, tb.tri_f);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, bool FULL>
+static cudaError_t launch_factored(const Geometry& g, const T* a, const T* c, const TriFactors<T>& tf, int parts,
+                                   int low, cplx<T>* spec, cudaStream_t st) {
+  int S = 256 / parts;
+  if (S < 1) S = 1;
+  if (S > 32) S = 32;
+  const size_t smem = (size_t)14 * parts * S * sizeof(T);
+  const int blocks = (tf.nsys + S - 1) / S;
+  auto kern = k_tridiag_factored<T, FULL>;
+  cudaError_t e;
+  if ((e = prep(kern, smem)) != cudaSuccess) return e;
+  kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, low, a, c, tf, spec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, cplx<double>* spec,
                                     cudaStream_t st) {
-  int S = 256 / parts;
-  if (S < 1) S = 1;
-  if (S > 32) S = 32;
-  const size_t smem = (size_t)14 * parts * S * sizeof(double);
-  const int blocks = (tb.tri.nsys + S - 1) / S;
-  auto kern = k_tridiag_factored;
-  cudaError_t e;
-  if ((e = prep(kern, smem)) != cudaSuccess) return e;
-  kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, tb.d.c, tb.tri, spec);
-  return cudaGetLastError();
+  return launch_factored<double, true>(g, tb.d.a, tb.d.c, tb.tri_d, parts, -1, spec, st);
+}
+
+cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                        cplx<float>* spec, cudaStream_t st) {
+  return launch_factored<float, false>(g, tb.f.a, tb.f.c, tb.tri_f, parts, low_modes, spec, st);
 }
 
 template <typename TD>
