@@ -15,11 +15,13 @@ namespace pp {
 
 struct Radix { int n; int r[8]; };
 
-// Factorisation preferring radix 16, then 8, 4, 2, with the factors of 3 last.
-__host__ __device__ constexpr Radix factorize(int L) {
+// Factorisation preferring radix 16 (when maxr allows), then 8, 4, 2, with the factors of 3
+// last.  FP64 kernels cap the radix at 8: a radix-16 butterfly stages 32 doubles per thread,
+// which halves their occupancy.
+__host__ __device__ constexpr Radix factorize(int L, int maxr = 16) {
   Radix f{0, {0, 0, 0, 0, 0, 0, 0, 0}};
   int x = L;
-  while (x % 16 == 0 && x > 8) { f.r[f.n++] = 16; x /= 16; }
+  while (maxr >= 16 && x % 16 == 0 && x > 8) { f.r[f.n++] = 16; x /= 16; }
   while (x % 8 == 0) { f.r[f.n++] = 8; x /= 8; }
   while (x % 4 == 0) { f.r[f.n++] = 4; x /= 4; }
   while (x % 2 == 0) { f.r[f.n++] = 2; x /= 2; }
@@ -32,9 +34,11 @@ __host__ __device__ constexpr bool factorizable(int L) {
   while (x % 3 == 0) x /= 3;
   return x == 1 && L > 1;
 }
-__host__ __device__ constexpr int span_before(int L, int s) {
+template <typename T> __host__ __device__ constexpr int max_radix() { return sizeof(T) == 4 ? 16 : 8; }
+
+__host__ __device__ constexpr int span_before(int L, int s, int maxr) {
   int ns = 1;
-  const Radix f = factorize(L);
+  const Radix f = factorize(L, maxr);
   for (int i = 0; i < s; ++i) ns *= f.r[i];
   return ns;
 }
@@ -91,9 +95,9 @@ template <typename T> __host__ __device__ constexpr int padded_size(int n) { ret
 // consecutive butterflies (rows).
 template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB>
 __device__ __forceinline__ void stage_inplace(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  constexpr Radix F = factorize(L);
+  constexpr Radix F = factorize(L, max_radix<T>());
   constexpr int R = F.r[S];
-  constexpr int Ns = span_before(L, S);
+  constexpr int Ns = span_before(L, S, max_radix<T>());
   constexpr int NBF = L / R;
   constexpr int TOTAL = NBF * B;
   constexpr int PER = (TOTAL + THREADS - 1) / THREADS;
@@ -137,7 +141,7 @@ __device__ __forceinline__ void stage_inplace(cplx<T>* buf, const cplx<T>* __res
 
 template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB>
 __device__ __forceinline__ void stages_from(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  constexpr Radix F = factorize(L);
+  constexpr Radix F = factorize(L, max_radix<T>());
   if constexpr (S < F.n) {
     stage_inplace<T, L, S, SIGN, B, THREADS, ES, BS, MAPB>(buf, tw);
     stages_from<T, L, S + 1, SIGN, B, THREADS, ES, BS, MAPB>(buf, tw);

@@ -81,6 +81,21 @@ template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
                          cudaStream_t st);
 
+// Specialised x-transforms for Nx/2 in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024}
+// (cudaErrorNotSupported otherwise).  Suffix: spectral type, field type (d = double, f = float).
+cudaError_t launch_fwd_x_fast_dd(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
+                                 cplx<double>* spec, cudaStream_t st);
+cudaError_t launch_fwd_x_fast_ff(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
+                                 cplx<float>* spec, cudaStream_t st);
+cudaError_t launch_fwd_x_fast_fd(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
+                                 cplx<float>* spec, cudaStream_t st);
+cudaError_t launch_inv_x_fast_dd(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<double>* spec,
+                                 double* out, double scale, bool accumulate, cudaStream_t st);
+cudaError_t launch_inv_x_fast_ff(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<float>* spec,
+                                 float* out, double scale, bool accumulate, cudaStream_t st);
+cudaError_t launch_inv_x_fast_fd(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<float>* spec,
+                                 double* out, double scale, bool accumulate, cudaStream_t st);
+
 // Specialised z-transform for Nz in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
 // returns cudaErrorNotSupported for other lengths.
 template <typename T>

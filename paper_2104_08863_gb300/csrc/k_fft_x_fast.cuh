@@ -1,0 +1,220 @@
+// Specialised x-transform kernels (steps (2) and (8) of Sec. 3.1) for the half-lengths
+// M = Nx/2 in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024}.
+//
+// A CTA takes LPB consecutive x-lines, which are one contiguous stretch of the field, packs
+// each real line as M complex values, transforms all lines in place in padded shared memory
+// with the compile-time Stockham engine, and unpacks the Nx/2+1 spectral bins (forward) or
+// writes the Nx real values (inverse).  LPB and the thread count give each thread 16 (FP32) or
+// 8 (FP64) staged complex values per stage.
+#pragma once
+
+#include "fft_static.cuh"
+#include "xline.cuh"
+
+namespace pp {
+
+template <typename T, int M> struct XTile {
+  static constexpr int E = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int LPB0 = (E * 256) / M;
+  static constexpr int LPB = LPB0 < 1 ? 1 : (LPB0 > 64 ? 64 : LPB0);
+  static constexpr int T0 = ((LPB * M / E) + 31) / 32 * 32;
+  static constexpr int THREADS = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
+  static constexpr int SMEM = padded_size<T>(LPB * M) * (int)sizeof(cplx<T>);
+  static constexpr int MINB = 2;
+};
+
+template <typename T, typename TI, int M, int MODE>
+__global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
+    k_fwd_x_fast(Geometry g, FwdArgs args, Tables<T> tt, DevTables tb, cplx<T>* __restrict__ spec, int nlines) {
+  using C = XTile<T, M>;
+  constexpr int LPB = C::LPB, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int line0 = blockIdx.x * LPB;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
+    const int t = idx / M, n = idx % M;
+    const int line = line0 + t;
+    buf[padi<T>(idx)] = line < nlines ? fwd_load<T, TI, MODE>(g, args, tt, tb, line, n) : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  fft_static<T, M, -1, LPB, THREADS, 1, M, false>(buf, tt.tw_m);
+  constexpr int M1 = M + 1;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
+    const int t = idx / M1, kx = idx % M1;
+    const int line = line0 + t;
+    if (line >= nlines) continue;
+    const cplx<T> Zk = buf[padi<T>(t * M + (kx == M ? 0 : kx))];
+    const cplx<T> Zc = conj(buf[padi<T>(t * M + (kx == 0 ? 0 : M - kx))]);
+    st_c(spec + (size_t)line * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+  }
+}
+
+template <typename T, typename TO, int M, int MODE, bool ACC>
+__global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
+    k_inv_x_fast(Geometry g, Tables<T> tt, const cplx<T>* __restrict__ spec, TO* __restrict__ out, double scl,
+                 int nlines, const double* __restrict__ dy, double* __restrict__ acc) {
+  using C = XTile<T, M>;
+  constexpr int LPB = C::LPB, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int line0 = blockIdx.x * LPB;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
+    const int t = idx / M, kx = idx % M;
+    const int line = line0 + t;
+    cplx<T> Z = mk<T>(T(0), T(0));
+    if (line < nlines) {
+      const cplx<T>* row = spec + (size_t)line * g.pitch;
+      Z = inv_pre(kx, ld_c(row + kx), ld_c(row + (M - kx)), ldg_c(tt.tw_post + kx));
+    }
+    buf[padi<T>(idx)] = Z;
+  }
+  __syncthreads();
+  fft_static<T, M, 1, LPB, THREADS, 1, M, false>(buf, tt.tw_m);
+  const T s = T(scl);
+  if constexpr (!ACC) {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
+      const int t = idx / M, n = idx % M;
+      const int line = line0 + t;
+      if (line >= nlines) continue;
+      const cplx<T> z = buf[padi<T>(idx)];
+      TO* o = out + (size_t)line * g.nx + 2 * n;
+      if constexpr (MODE == INV_ACCUM) {
+        TO a, b;
+        RealIO<TO>::load2(o, a, b);
+        RealIO<TO>::store2(o, a + TO(z.x * s), b + TO(z.y * s));
+      } else {
+        RealIO<TO>::store2(o, TO(z.x * s), TO(z.y * s));
+      }
+    }
+  } else {
+    // one warp per line: the line's dy-weighted sum is reduced with compensated sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NWARPS = THREADS / 32;
+    double wsum = 0.0;
+    for (int t = warp; t < LPB; t += NWARPS) {
+      const int line = line0 + t;
+      if (line >= nlines) break;
+      T hs = T(0), hc = T(0);
+      for (int n = lane; n < M; n += 32) {
+        const cplx<T> z = buf[padi<T>(t * M + n)];
+        const T x0 = z.x * s, x1 = z.y * s;
+        TO* o = out + (size_t)line * g.nx + 2 * n;
+        if constexpr (MODE == INV_ACCUM) {
+          TO a, b;
+          RealIO<TO>::load2(o, a, b);
+          RealIO<TO>::store2(o, a + TO(x0), b + TO(x1));
+        } else {
+          RealIO<TO>::store2(o, TO(x0), TO(x1));
+        }
+        acc_add(hs, hc, x0);
+        acc_add(hs, hc, x1);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T os = __shfl_xor_sync(0xffffffffu, hs, o), oc = __shfl_xor_sync(0xffffffffu, hc, o);
+        T e;
+        if constexpr (sizeof(T) == 4) {
+          two_sum(hs, os, hs, e);
+        } else {
+          hs += os;
+          e = T(0);
+        }
+        hc += oc + e;
+      }
+      if (lane == 0) wsum += dy[line / g.nz] * ((double)hs + (double)hc);
+    }
+    if (lane == 0 && wsum != 0.0) atomicAdd(acc + 1, wsum);
+  }
+}
+
+template <typename K>
+inline cudaError_t set_smem(K kernel, int smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename T, typename TI, int M>
+cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
+                           const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
+  using C = XTile<T, M>;
+  const int nlines = g.ny * g.nz;
+  const dim3 grid((nlines + C::LPB - 1) / C::LPB);
+  cudaError_t e = cudaSuccess;
+#define PP_FWDF(MODEV)                                                                  \
+  {                                                                                     \
+    auto k = k_fwd_x_fast<T, TI, M, MODEV>;                                             \
+    if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                            \
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, args, tt, tb, spec, nlines);                \
+  }
+  if constexpr (sizeof(T) == sizeof(TI)) {
+    switch (mode) {
+      case FWD_PLAIN: PP_FWDF(FWD_PLAIN) break;
+      case FWD_DIV: PP_FWDF(FWD_DIV) break;
+      case FWD_GRADT: PP_FWDF(FWD_GRADT) break;
+      default: return cudaErrorNotSupported;
+    }
+  } else {
+    switch (mode) {
+      case FWD_PLAIN: PP_FWDF(FWD_PLAIN) break;
+      case FWD_RESID: PP_FWDF(FWD_RESID) break;
+      default: return cudaErrorNotSupported;
+    }
+  }
+#undef PP_FWDF
+  return cudaGetLastError();
+}
+
+template <typename T, typename TO, int M>
+cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
+                           const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
+  using C = XTile<T, M>;
+  const int nlines = g.ny * g.nz;
+  const dim3 grid((nlines + C::LPB - 1) / C::LPB);
+  cudaError_t e = cudaSuccess;
+#define PP_INVF(MODEV, ACCV)                                                                     \
+  {                                                                                              \
+    auto k = k_inv_x_fast<T, TO, M, MODEV, ACCV>;                                                \
+    if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                                     \
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, out, scale, nlines, tb.dy, tb.acc);       \
+  }
+  if constexpr (sizeof(T) == sizeof(TO)) {
+    if (mode != INV_STORE || accumulate) return cudaErrorNotSupported;
+    PP_INVF(INV_STORE, false)
+  } else {
+    if (!accumulate) return cudaErrorNotSupported;
+    if (mode == INV_ACCUM) PP_INVF(INV_ACCUM, true) else PP_INVF(INV_STORE, true)
+  }
+#undef PP_INVF
+  return cudaGetLastError();
+}
+
+#define PP_X_SIZES(F) F(16) F(32) F(48) F(64) F(96) F(128) F(192) F(256) F(384) F(512) F(768) F(1024)
+
+template <typename T, typename TI>
+cudaError_t launch_fwd_x_fast_impl(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
+                                   const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
+  switch (g.M) {
+#define PP_CASE(MV) \
+  case MV: return launch_fwd_x_m<T, TI, MV>(g, tb, tt, mode, args, spec, st);
+    PP_X_SIZES(PP_CASE)
+#undef PP_CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename T, typename TO>
+cudaError_t launch_inv_x_fast_impl(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
+                                   const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
+  switch (g.M) {
+#define PP_CASE(MV) \
+  case MV: return launch_inv_x_m<T, TO, MV>(g, tb, tt, mode, spec, out, scale, accumulate, st);
+    PP_X_SIZES(PP_CASE)
+#undef PP_CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace pp

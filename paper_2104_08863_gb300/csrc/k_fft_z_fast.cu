@@ -17,7 +17,7 @@ template <typename T, int NZ> struct ZTile {
   static constexpr int T0 = W * NZ / E;
   static constexpr int THREADS = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
   static constexpr int SMEM = padded_size<T>(W * NZ) * (int)sizeof(cplx<T>);
-  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;   // FP32: two CTAs per SM (<= 64 registers)
+  static constexpr int MINB = 2;   // two CTAs per SM so one CTA's memory phase overlaps the other's math
 };
 
 template <typename T, int NZ, int SIGN>
