@@ -85,6 +85,10 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
   dt.d.inv_h = (const double*)(tb + to[15]);
   dt.f.inv_dy = (const float*)(tb + to[16]);
   dt.f.inv_h = (const float*)(tb + to[17]);
+  dt.f.a_lo = (const float*)(tb + to[18]);
+  dt.f.c_lo = (const float*)(tb + to[19]);
+  dt.d.a_lo = nullptr;
+  dt.d.c_lo = nullptr;
   dt.status = (int*)(base + pl->off_status);
   dt.acc = (double*)(base + pl->off_acc);
   dt.tri_d = TriFactors<double>{};
@@ -217,6 +221,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   slot(12, 8 * (size_t)ny);   slot(13, 8 * (size_t)(ny + 1));
   slot(14, 8 * (size_t)ny);   slot(15, 8 * (size_t)(ny + 1));
   slot(16, 4 * (size_t)ny);   slot(17, 4 * (size_t)(ny + 1));
+  slot(18, 4 * (size_t)ny);   slot(19, 4 * (size_t)ny);
   const size_t tab_bytes = off;
   pl->host_tables.assign(tab_bytes, 0);
   auto& img = pl->host_tables;
@@ -241,6 +246,15 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   put_real_table<double>(img, to[15], inv_h);
   put_real_table<float>(img, to[16], inv_dy);
   put_real_table<float>(img, to[17], inv_h);
+  {   // low parts of the double-float coefficients (a, c) used by the refinement residual
+    std::vector<double> alo(ny), clo(ny);
+    for (int j = 0; j < ny; ++j) {
+      alo[j] = pl->a[j] - (double)(float)pl->a[j];
+      clo[j] = pl->c[j] - (double)(float)pl->c[j];
+    }
+    put_real_table<float>(img, to[18], alo);
+    put_real_table<float>(img, to[19], clo);
+  }
 
   // --- workspace layout ---
   const size_t csz = spec_is_fp64(pl) ? 16 : 8;
@@ -248,6 +262,8 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   off = 0;
   pl->off_spec = off;  off = align_up(off + csz * (size_t)ny * g.nz * g.pitch, 256);
   pl->off_pbuf = off;  off = align_up(off + rsz * (size_t)ny * g.nz * g.nx, 256);
+  pl->off_pbuf2 = off;   // low FP32 part of the refined pressure
+  if (d->precision == PP_FP32_REFINED) off = align_up(off + 4 * (size_t)ny * g.nz * g.nx, 256);
   pl->off_scratch = off;
   if (L >= 0) off = align_up(off + 16 * (size_t)ny * (L + 1) * (2 * L + 1), 256);
   pl->off_tables = off; off = align_up(off + tab_bytes, 256);
@@ -384,12 +400,17 @@ poisson_status forward_and_core(Exec& ex, FwdMode mode, const FwdArgs& args, Gau
 }
 
 template <typename T, typename TO>
-poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate) {
+poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate, PairArgs pair = PairArgs{nullptr, nullptr}) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   const double scale = 1.0 / ((double)ex.pl->g.nx * (double)ex.pl->g.nz);
   cudaStream_t st = ex.st;
-  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st)));
+  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st, pair)));
   return PS_OK;
+}
+
+void split_f32(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
 }
 
 size_t cell_count(const poisson_plan_s* pl) { return (size_t)pl->g.ny * pl->g.nz * pl->g.nx; }
@@ -405,11 +426,16 @@ poisson_status check_finite(Exec& ex, const void* x, size_t n) {
 
 // The solve of poisson_solve on any workspace (caller-owned or the library's static one).
 //
-// PP_FP32_REFINED: p_0 = S32 f; then refine_steps times  r = (f - <f>) - L_h p  (FP64),
-// p += S32 r.  <f> is taken from the first solve's (0, 0) mode so that the FP32 transform of
-// r carries no large constant; the weighted sum of p is accumulated by every inverse pass and
-// each correction's (0, 0) mode cancels it, so the gauge error of the FP32 transforms does not
-// persist (the residual cannot see a constant).
+// PP_FP32_REFINED keeps the pressure as an FP32 pair p = hi + lo in the workspace and never
+// issues per-point FP64 arithmetic (slow on GB300):
+//   hi = S32 f;  then for each of refine_steps corrections
+//   r = (f - <f>) - L_h (hi + lo) in double-float arithmetic;  d = S32 r;
+//   lo = d (first) or lo += d, and on the last correction p = hi + (lo + d) is written in FP64
+//   by exact integer assembly.
+// <f> is taken from the first solve's (0, 0) mode so that the FP32 transform of r carries no
+// large constant; the dy-weighted sum of p is accumulated by every inverse pass and each
+// correction's (0, 0) mode cancels it, so the gauge error of the FP32 transforms (invisible to
+// the residual) does not persist.
 poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
   const poisson_plan_s* pl = ex.pl;
   FwdArgs args = {};
@@ -424,17 +450,27 @@ poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
     PP_RET((forward_and_core<float, float>(ex, FWD_PLAIN, args, GAUGE_ZERO)));
     PP_RET((inverse_x<float, float>(ex, INV_STORE, (float*)p, false)));
   } else {
+    float* hi = (float*)(ex.ws + pl->off_pbuf);
+    float* lo = (float*)(ex.ws + pl->off_pbuf2);
     PP_RET(check_finite<double>(ex, rhs, cell_count(pl)));
     if (cudaMemsetAsync(ex.dt.acc, 0, 2 * sizeof(double), ex.st) != cudaSuccess) return PS_ECUDA;
     PP_RET((forward_and_core<float, double>(ex, FWD_PLAIN, args, GAUGE_STORE_MEAN)));
-    PP_RET((inverse_x<float, double>(ex, INV_STORE, (double*)p, true)));
-    for (int r = 0; r < pl->refine; ++r) {
-      FwdArgs ra = {};
-      ra.in = rhs;
-      ra.p = p;
-      ra.in_scale = 1.0;
+    PP_RET((inverse_x<float, float>(ex, INV_STORE, hi, true)));
+    FwdArgs ra = {};
+    ra.in = rhs;
+    ra.p = hi;
+    ra.in_scale = 1.0;
+    split_f32(1.0 / (pl->g.dx * pl->g.dx), ra.idx2h, ra.idx2l);
+    split_f32(1.0 / (pl->g.dz * pl->g.dz), ra.idz2h, ra.idz2l);
+    for (int r = 1; r <= pl->refine; ++r) {
+      ra.plo = r >= 2 ? lo : nullptr;
       PP_RET((forward_and_core<float, double>(ex, FWD_RESID, ra, GAUGE_OFFSET)));
-      PP_RET((inverse_x<float, double>(ex, INV_ACCUM, (double*)p, true)));
+      if (r < pl->refine) {
+        PP_RET((inverse_x<float, float>(ex, r == 1 ? INV_STORE : INV_ACCUM, lo, true)));
+      } else {
+        PairArgs pair{hi, r >= 2 ? lo : nullptr};
+        PP_RET((inverse_x<float, double>(ex, INV_FINAL, (double*)p, true, pair)));
+      }
     }
   }
   return PS_OK;

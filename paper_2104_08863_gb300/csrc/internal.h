@@ -19,6 +19,8 @@ template <typename T> struct Tables {
   const T* c;              // wall-normal super-diagonal c_j (0 for j = ny-1)
   const T* inv_dy;         // 1 / dy_j
   const T* inv_h;          // 1 / h_j for interior faces j = 1..ny-1, 0 on the walls
+  const T* a_lo;           // FP32 tables only: a_j - (float)a_j, so (a, a_lo) is a double-float
+  const T* c_lo;           // FP32 tables only: c_j - (float)c_j
 };
 
 // Per-mode PDD factors, built once by k_tridiag_setup (layout [row][system]
@@ -57,15 +59,26 @@ struct LaunchCount {
 
 // --- launchers (return cudaGetLastError() after the launch) --------------------------
 enum FwdMode { FWD_PLAIN = 0, FWD_DIV = 1, FWD_RESID = 2, FWD_GRADT = 3 };
-enum InvMode { INV_STORE = 0, INV_ACCUM = 1, INV_ADJ = 2 };
+// INV_FINAL (FP32 spectrum, FP64 output): out = hi + (lo + v) assembled exactly in FP64,
+// with hi, lo the FP32 pair that carries the refined pressure (lo may be null).
+enum InvMode { INV_STORE = 0, INV_ACCUM = 1, INV_FINAL = 2 };
 
 struct FwdArgs {
   const void* in;        // FWD_PLAIN / FWD_RESID: rhs field
   const void* u;         // FWD_DIV / FWD_GRADT: face fields
   const void* v;
   const void* w;
-  const void* p;         // FWD_RESID: current pressure (FP64)
-  double in_scale;       // FWD_DIV: 1/dt; FWD_PLAIN: 1
+  const void* p;         // FWD_RESID: pressure, high FP32 part
+  const void* plo;       // FWD_RESID: pressure, low FP32 part (may be null)
+  double in_scale;       // FWD_DIV: 1/dt; FWD_PLAIN: 1 (ignored for FP64 input to FP32)
+  float idx2h, idx2l;    // FWD_RESID: 1/dx^2 and 1/dz^2 as double-floats
+  float idz2h, idz2l;
+};
+
+// Pointers of the FP32 pressure pair used by INV_FINAL.
+struct PairArgs {
+  const float* hi;
+  const float* lo;
 };
 
 template <typename T, typename TI>
@@ -75,7 +88,8 @@ cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactor
 // accumulate: also add sum_jki dy_j out_jki (of this pass's contribution) to tb.acc[1].
 template <typename T, typename TO>
 cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
-                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st);
+                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                         PairArgs pair = PairArgs{nullptr, nullptr});
 
 template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
@@ -90,11 +104,11 @@ cudaError_t launch_fwd_x_fast_ff(const Geometry& g, const DevTables& tb, FwdMode
 cudaError_t launch_fwd_x_fast_fd(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
                                  cplx<float>* spec, cudaStream_t st);
 cudaError_t launch_inv_x_fast_dd(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<double>* spec,
-                                 double* out, double scale, bool accumulate, cudaStream_t st);
+                                 double* out, double scale, bool accumulate, cudaStream_t st, PairArgs pair);
 cudaError_t launch_inv_x_fast_ff(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<float>* spec,
-                                 float* out, double scale, bool accumulate, cudaStream_t st);
+                                 float* out, double scale, bool accumulate, cudaStream_t st, PairArgs pair);
 cudaError_t launch_inv_x_fast_fd(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<float>* spec,
-                                 double* out, double scale, bool accumulate, cudaStream_t st);
+                                 double* out, double scale, bool accumulate, cudaStream_t st, PairArgs pair);
 
 // Specialised z-transform for Nz in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
 // returns cudaErrorNotSupported for other lengths.
@@ -154,7 +168,7 @@ struct poisson_plan_s {
   std::vector<double> faces, dy, h, a, c, lamx, lamz;
   std::vector<unsigned char> host_tables;   // staging image of the device tables
   // workspace layout (byte offsets)
-  size_t off_spec, off_pbuf, off_scratch, off_tables, off_status, off_acc, off_tri, ws_bytes;
+  size_t off_spec, off_pbuf, off_pbuf2, off_scratch, off_tables, off_status, off_acc, off_tri, ws_bytes;
   size_t tab_offsets[32];
   unsigned char* ws;
   pp::DevTables dt;

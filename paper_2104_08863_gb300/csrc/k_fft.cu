@@ -45,7 +45,7 @@ template <typename T, typename TO, int MODE, bool ACC>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, Tables<T> tt, FftFactors fm,
                                                const cplx<T>* __restrict__ spec, TO* __restrict__ out, double scl,
                                                int lpb, int nlines, const double* __restrict__ dy,
-                                               double* __restrict__ acc) {
+                                               double* __restrict__ acc, PairArgs pair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = fm.L;
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -74,14 +74,8 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, Tables<T> tt, FftFact
     for (int n = lane; n < M; n += 32) {
       const cplx<T> z = res[t * M + n];
       const T x0 = z.x * s, x1 = z.y * s;
-      TO* o = out + (size_t)line * g.nx + 2 * n;
-      if (MODE == INV_ACCUM) {
-        TO a, b;
-        RealIO<TO>::load2(o, a, b);
-        RealIO<TO>::store2(o, a + TO(x0), b + TO(x1));
-      } else {
-        RealIO<TO>::store2(o, TO(x0), TO(x1));
-      }
+      const size_t off = (size_t)line * g.nx + 2 * n;
+      inv_store<T, TO, MODE>(out + off, off, x0, x1, pair);
       if (ACC) {
         acc_add(hs, hc, x0);
         acc_add(hs, hc, x1);
@@ -180,15 +174,16 @@ cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactor
 
 template <typename T, typename TO>
 cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
-                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
+                         const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                         PairArgs pair) {
   {
     cudaError_t ef;
     if constexpr (sizeof(T) == 8)
-      ef = launch_inv_x_fast_dd(g, tb, mode, (const cplx<double>*)spec, (double*)out, scale, accumulate, st);
+      ef = launch_inv_x_fast_dd(g, tb, mode, (const cplx<double>*)spec, (double*)out, scale, accumulate, st, pair);
     else if constexpr (sizeof(TO) == 4)
-      ef = launch_inv_x_fast_ff(g, tb, mode, (const cplx<float>*)spec, (float*)out, scale, accumulate, st);
+      ef = launch_inv_x_fast_ff(g, tb, mode, (const cplx<float>*)spec, (float*)out, scale, accumulate, st, pair);
     else
-      ef = launch_inv_x_fast_fd(g, tb, mode, (const cplx<float>*)spec, (double*)out, scale, accumulate, st);
+      ef = launch_inv_x_fast_fd(g, tb, mode, (const cplx<float>*)spec, (double*)out, scale, accumulate, st, pair);
     if (ef != cudaErrorNotSupported) return ef;
   }
   const int nlines = g.ny * g.nz;
@@ -200,9 +195,15 @@ cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactor
   {                                                                                                       \
     auto kern = k_inv_x<T, TO, MODEV, ACCV>;                                                              \
     if ((e = prep(kern, smem)) != cudaSuccess) return e;                                                  \
-    kern<<<grid, 256, smem, st>>>(g, tabs<T>(tb), fm, spec, out, scale, lpb, nlines, tb.dy, tb.acc);     \
+    kern<<<grid, 256, smem, st>>>(g, tabs<T>(tb), fm, spec, out, scale, lpb, nlines, tb.dy, tb.acc, pair); \
   }
-  if (mode == INV_ACCUM) {
+  if (mode == INV_FINAL) {
+    if constexpr (sizeof(T) == 4 && sizeof(TO) == 8) {
+      if (accumulate) PP_INV(INV_FINAL, true) else PP_INV(INV_FINAL, false)
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  } else if (mode == INV_ACCUM) {
     if (accumulate) PP_INV(INV_ACCUM, true) else PP_INV(INV_ACCUM, false)
   } else {
     if (accumulate) PP_INV(INV_STORE, true) else PP_INV(INV_STORE, false)
@@ -243,11 +244,14 @@ template cudaError_t launch_fwd_x<float, float>(const Geometry&, const DevTables
 template cudaError_t launch_fwd_x<float, double>(const Geometry&, const DevTables&, const FftFactors&, FwdMode,
                                                  const FwdArgs&, cplx<float>*, cudaStream_t);
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                  const cplx<double>*, double*, double, bool, cudaStream_t);
+                                                  const cplx<double>*, double*, double, bool, cudaStream_t,
+                                                  PairArgs);
 template cudaError_t launch_inv_x<float, float>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                const cplx<float>*, float*, double, bool, cudaStream_t);
+                                                const cplx<float>*, float*, double, bool, cudaStream_t,
+                                                  PairArgs);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DevTables&, const FftFactors&, InvMode,
-                                                 const cplx<float>*, double*, double, bool, cudaStream_t);
+                                                 const cplx<float>*, double*, double, bool, cudaStream_t,
+                                                  PairArgs);
 template cudaError_t launch_fft_z<double>(const Geometry&, const DevTables&, const FftFactors&, int, cplx<double>*,
                                           cudaStream_t);
 template cudaError_t launch_fft_z<float>(const Geometry&, const DevTables&, const FftFactors&, int, cplx<float>*,

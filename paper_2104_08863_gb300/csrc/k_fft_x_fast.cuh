@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
 template <typename T, typename TO, int M, int MODE, bool ACC>
 __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
     k_inv_x_fast(Geometry g, Tables<T> tt, const cplx<T>* __restrict__ spec, TO* __restrict__ out, double scl,
-                 int nlines, const double* __restrict__ dy, double* __restrict__ acc) {
+                 int nlines, const double* __restrict__ dy, double* __restrict__ acc, PairArgs pair) {
   using C = XTile<T, M>;
   constexpr int LPB = C::LPB, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -81,14 +81,8 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
       const int line = line0 + t;
       if (line >= nlines) continue;
       const cplx<T> z = buf[padi<T>(idx)];
-      TO* o = out + (size_t)line * g.nx + 2 * n;
-      if constexpr (MODE == INV_ACCUM) {
-        TO a, b;
-        RealIO<TO>::load2(o, a, b);
-        RealIO<TO>::store2(o, a + TO(z.x * s), b + TO(z.y * s));
-      } else {
-        RealIO<TO>::store2(o, TO(z.x * s), TO(z.y * s));
-      }
+      const size_t off = (size_t)line * g.nx + 2 * n;
+      inv_store<T, TO, MODE>(out + off, off, z.x * s, z.y * s, pair);
     }
   } else {
     // one warp per line: the line's dy-weighted sum is reduced with compensated sums
@@ -102,14 +96,8 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
       for (int n = lane; n < M; n += 32) {
         const cplx<T> z = buf[padi<T>(t * M + n)];
         const T x0 = z.x * s, x1 = z.y * s;
-        TO* o = out + (size_t)line * g.nx + 2 * n;
-        if constexpr (MODE == INV_ACCUM) {
-          TO a, b;
-          RealIO<TO>::load2(o, a, b);
-          RealIO<TO>::store2(o, a + TO(x0), b + TO(x1));
-        } else {
-          RealIO<TO>::store2(o, TO(x0), TO(x1));
-        }
+        const size_t off = (size_t)line * g.nx + 2 * n;
+        inv_store<T, TO, MODE>(out + off, off, x0, x1, pair);
         acc_add(hs, hc, x0);
         acc_add(hs, hc, x1);
       }
@@ -169,7 +157,8 @@ cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<
 
 template <typename T, typename TO, int M>
 cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
-                           const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
+                           const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                           PairArgs pair) {
   using C = XTile<T, M>;
   const int nlines = g.ny * g.nz;
   const dim3 grid((nlines + C::LPB - 1) / C::LPB);
@@ -178,14 +167,18 @@ cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<
   {                                                                                              \
     auto k = k_inv_x_fast<T, TO, M, MODEV, ACCV>;                                                \
     if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                                     \
-    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, out, scale, nlines, tb.dy, tb.acc);       \
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, out, scale, nlines, tb.dy, tb.acc, pair); \
   }
   if constexpr (sizeof(T) == sizeof(TO)) {
-    if (mode != INV_STORE || accumulate) return cudaErrorNotSupported;
-    PP_INVF(INV_STORE, false)
+    if (mode == INV_FINAL) return cudaErrorNotSupported;
+    if (mode == INV_ACCUM) {
+      if (accumulate) PP_INVF(INV_ACCUM, true) else PP_INVF(INV_ACCUM, false)
+    } else {
+      if (accumulate) PP_INVF(INV_STORE, true) else PP_INVF(INV_STORE, false)
+    }
   } else {
-    if (!accumulate) return cudaErrorNotSupported;
-    if (mode == INV_ACCUM) PP_INVF(INV_ACCUM, true) else PP_INVF(INV_STORE, true)
+    if (mode != INV_FINAL || !accumulate) return cudaErrorNotSupported;
+    PP_INVF(INV_FINAL, true)
   }
 #undef PP_INVF
   return cudaGetLastError();
@@ -207,10 +200,11 @@ cudaError_t launch_fwd_x_fast_impl(const Geometry& g, const DevTables& tb, const
 
 template <typename T, typename TO>
 cudaError_t launch_inv_x_fast_impl(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
-                                   const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st) {
+                                   const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                                   PairArgs pair) {
   switch (g.M) {
 #define PP_CASE(MV) \
-  case MV: return launch_inv_x_m<T, TO, MV>(g, tb, tt, mode, spec, out, scale, accumulate, st);
+  case MV: return launch_inv_x_m<T, TO, MV>(g, tb, tt, mode, spec, out, scale, accumulate, st, pair);
     PP_X_SIZES(PP_CASE)
 #undef PP_CASE
     default: return cudaErrorNotSupported;

@@ -4,6 +4,7 @@
 // its inverse, and compensated sums.
 #pragma once
 
+#include "fpconv.cuh"
 #include "internal.h"
 
 namespace pp {
@@ -63,35 +64,55 @@ __device__ __forceinline__ void gradT_pair(const Geometry& g, const TI* __restri
   f1 = ((u1 - u2) * inv_dx + (w0[i0 + 1] - w1[i0 + 1]) * inv_dz + ty1) * inv_dy;
 }
 
-// (f - <f>) - L_h p at cells (j,k,i0), (j,k,i0+1), FP64 (refinement residual).  Removing the
-// mean of f here keeps the FP32 transform of the residual free of a large constant whose
-// rounding noise would otherwise leak into the weakly damped low modes at every step.
-__device__ __forceinline__ void residual_pair(const Geometry& g, const double* __restrict__ f,
-                                              const double* __restrict__ p, int j, int k, int i0, double idx2,
-                                              double idz2, double aj, double cj, double fmean, double& r0,
-                                              double& r1) {
-  const size_t nx = g.nx;
+// Refinement residual r = (f - <f>) - L_h p at cells (j,k,i0) and (j,k,i0+1), where f is the
+// FP64 right-hand side and p = hi + lo the pressure carried as an FP32 pair.  Removing <f>
+// keeps the FP32 transform of r free of a large constant whose rounding noise would otherwise
+// leak into the weakly damped low modes at every step.  L_h p is formed in double-float
+// arithmetic on FP32 units: neighbour differences of hi are exact (TwoDiff) and those of lo are
+// added in double-float (near the walls the stencil terms of lo cancel strongly, so plain FP32
+// would floor the refinement), products with the double-float stencil coefficients recover
+// their rounding error with FMAs, and the sums carry a compensation term, so r is accurate to
+// ~2^-47 of the stencil terms.
+template <typename TT>
+__device__ __forceinline__ void residual_pair_df(const Geometry& g, const FwdArgs& args, const TT& tt,
+                                                 const DevTables& tb, int j, int k, int i0, float& r0, float& r1) {
+  const size_t nx = g.nx, plane = (size_t)g.nz * nx;
   const size_t row = ((size_t)j * g.nz + k) * nx;
-  const double* pr = p + row;
-  const double* pkm = p + ((size_t)j * g.nz + (k == 0 ? g.nz - 1 : k - 1)) * nx;
-  const double* pkp = p + ((size_t)j * g.nz + (k + 1 == g.nz ? 0 : k + 1)) * nx;
+  const size_t rkm = ((size_t)j * g.nz + (k == 0 ? g.nz - 1 : k - 1)) * nx;
+  const size_t rkp = ((size_t)j * g.nz + (k + 1 == g.nz ? 0 : k + 1)) * nx;
   const int im = i0 == 0 ? g.nx - 1 : i0 - 1;
   const int ip = i0 + 2 == g.nx ? 0 : i0 + 2;
-  const double pm = pr[im], p0 = pr[i0], p1 = pr[i0 + 1], pp = pr[ip];
-  double l0 = (pm - 2.0 * p0 + p1) * idx2 + (pkm[i0] - 2.0 * p0 + pkp[i0]) * idz2;
-  double l1 = (p0 - 2.0 * p1 + pp) * idx2 + (pkm[i0 + 1] - 2.0 * p1 + pkp[i0 + 1]) * idz2;
-  if (j >= 1) {
-    const double* pl = pr - (size_t)g.nz * nx;
-    l0 += aj * (pl[i0] - p0);
-    l1 += aj * (pl[i0 + 1] - p1);
+  const bool has_lo = j >= 1, has_hi = j + 1 <= g.ny - 1;
+  const df cx{args.idx2h, args.idx2l}, cz{args.idz2h, args.idz2l};
+  const df ca{tt.a[j], tt.a_lo[j]}, cc{tt.c[j], tt.c_lo[j]};
+  float mh, ml;
+  f64_split(tb.acc[0], mh, ml);
+  const float* P = reinterpret_cast<const float*>(args.p);
+  const float* Q = reinterpret_cast<const float*>(args.plo);
+  const double* f = reinterpret_cast<const double*>(args.in);
+  // neighbour difference d(n) = p_n - p_c of p = hi + lo, exact in hi and carried in double-float
+  auto diff = [&](size_t n, size_t o) -> df {
+    df d = two_diff_df(P[n], P[o]);
+    if (Q) d = df_add(d, two_diff_df(Q[n], Q[o]));
+    return d;
+  };
+  float out[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const size_t o = row + i0 + c;
+    const size_t xm = row + (c == 0 ? im : i0), xp = row + (c == 0 ? i0 + 1 : ip);
+    df L = df_mul(df_add(diff(xp, o), diff(xm, o)), cx);
+    L = df_add(L, df_mul(df_add(diff(rkp + i0 + c, o), diff(rkm + i0 + c, o)), cz));
+    if (has_lo) L = df_add(L, df_mul(diff(o - plane, o), ca));
+    if (has_hi) L = df_add(L, df_mul(diff(o + plane, o), cc));
+    float fh, fl;
+    f64_split(f[o], fh, fl);
+    df r = df_add(df{fh, fl}, df{-mh, -ml});
+    r = df_add(r, df_neg(L));
+    out[c] = r.hi + r.lo;
   }
-  if (j + 1 <= g.ny - 1) {
-    const double* pu = pr + (size_t)g.nz * nx;
-    l0 += cj * (pu[i0] - p0);
-    l1 += cj * (pu[i0 + 1] - p1);
-  }
-  r0 = (f[row + i0] - fmean) - l0;
-  r1 = (f[row + i0 + 1] - fmean) - l1;
+  r0 = out[0];
+  r1 = out[1];
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -121,8 +142,13 @@ __device__ __forceinline__ cplx<T> fwd_load(const Geometry& g, const FwdArgs& ar
   if constexpr (MODE == FWD_PLAIN) {
     TI a, b;
     RealIO<TI>::load2(reinterpret_cast<const TI*>(args.in) + (size_t)line * g.nx + i0, a, b);
-    const TI s = TI(args.in_scale);
-    return mk<T>(T(a * s), T(b * s));
+    if constexpr (sizeof(T) < sizeof(TI)) {
+      // FP64 input to the FP32 solve: integer truncation keeps the FP64 pipe idle
+      return mk<T>(f64_to_f32_trunc(a), f64_to_f32_trunc(b));
+    } else {
+      const TI s = TI(args.in_scale);
+      return mk<T>(T(a * s), T(b * s));
+    }
   } else if constexpr (MODE == FWD_DIV) {
     TI f0, f1;
     const TI s = TI(args.in_scale);
@@ -136,11 +162,14 @@ __device__ __forceinline__ cplx<T> fwd_load(const Geometry& g, const FwdArgs& ar
                    reinterpret_cast<const TI*>(args.w), j, k, i0, TI(1.0 / g.dx), TI(1.0 / g.dz),
                    TI(tt.inv_h[j]), TI(tt.inv_h[j + 1]), TI(tt.inv_dy[j]), f0, f1);
     return mk<T>(T(f0), T(f1));
-  } else {  // FWD_RESID (FP64 operands)
-    double r0, r1;
-    residual_pair(g, reinterpret_cast<const double*>(args.in), reinterpret_cast<const double*>(args.p), j, k, i0,
-                  1.0 / (g.dx * g.dx), 1.0 / (g.dz * g.dz), tb.d.a[j], tb.d.c[j], tb.acc[0], r0, r1);
-    return mk<T>(T(r0), T(r1));
+  } else {  // FWD_RESID: FP64 rhs, FP32-pair pressure, double-float arithmetic
+    if constexpr (sizeof(T) == 4) {
+      float r0, r1;
+      residual_pair_df(g, args, tt, tb, j, k, i0, r0, r1);
+      return mk<T>(r0, r1);
+    } else {
+      return mk<T>(T(0), T(0));   // not used: the FP64 path never refines
+    }
   }
 }
 
@@ -160,6 +189,26 @@ __device__ __forceinline__ cplx<T> inv_pre(int kx, cplx<T> Xk, cplx<T> Xm, cplx<
   const cplx<T> Xc = conj(Xm);
   const cplx<T> s = Xk + Xc, d = Xk - Xc;
   return s + mul_i(cmulc(d, W), 1);   // i conj(W) (Xk - Xc)
+}
+
+// Epilogue of the inverse x-transform: store, accumulate, or (INV_FINAL) assemble the FP64
+// pressure hi + (lo + v) of the refined solve exactly by integer arithmetic.
+template <typename T, typename TO, int MODE>
+__device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const PairArgs& pair) {
+  if constexpr (MODE == INV_ACCUM) {
+    TO a, b;
+    RealIO<TO>::load2(o, a, b);
+    RealIO<TO>::store2(o, a + TO(x0), b + TO(x1));
+  } else if constexpr (MODE == INV_FINAL) {
+    if constexpr (sizeof(T) == 4 && sizeof(TO) == 8) {
+      const float2 h = *reinterpret_cast<const float2*>(pair.hi + off);
+      float2 l = make_float2(0.0f, 0.0f);
+      if (pair.lo) l = *reinterpret_cast<const float2*>(pair.lo + off);
+      RealIO<TO>::store2(o, f32_pair_to_f64(h.x, l.x + x0), f32_pair_to_f64(h.y, l.y + x1));
+    }
+  } else {
+    RealIO<TO>::store2(o, TO(x0), TO(x1));
+  }
 }
 
 }  // namespace pp
