@@ -31,11 +31,30 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int line0 = blockIdx.x * LPB;
+  if constexpr (MODE == FWD_RESID && sizeof(T) == 4) {
+    // refinement residual: per-line setup, then pairs of cells
+    float mh, ml;
+    f64_split(tb.acc[0], mh, ml);
+    for (int t = 0; t < LPB; ++t) {
+      const int line = line0 + t;
+      if (line < nlines) {
+        const ResidLine R = resid_line(g, args, tt, tb, line, mh, ml);
+#pragma unroll
+        for (int n = threadIdx.x; n < M; n += THREADS) {
+          const float2 r = resid_pair_line(R, n);
+          buf[padi<T>(t * M + n)] = mk<T>(r.x, r.y);
+        }
+      } else {
+        for (int n = threadIdx.x; n < M; n += THREADS) buf[padi<T>(t * M + n)] = mk<T>(T(0), T(0));
+      }
+    }
+  } else {
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
-    const int t = idx / M, n = idx % M;
-    const int line = line0 + t;
-    buf[padi<T>(idx)] = line < nlines ? fwd_load<T, TI, MODE>(g, args, tt, tb, line, n) : mk<T>(T(0), T(0));
+    for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
+      const int t = idx / M, n = idx % M;
+      const int line = line0 + t;
+      buf[padi<T>(idx)] = line < nlines ? fwd_load<T, TI, MODE>(g, args, tt, tb, line, n) : mk<T>(T(0), T(0));
+    }
   }
   __syncthreads();
   fft_static<T, M, -1, LPB, THREADS, 1, M, false>(buf, tt.tw_m);
@@ -93,6 +112,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
       const int line = line0 + t;
       if (line >= nlines) break;
       T hs = T(0), hc = T(0);
+#pragma unroll 4
       for (int n = lane; n < M; n += 32) {
         const cplx<T> z = buf[padi<T>(t * M + n)];
         const T x0 = z.x * s, x1 = z.y * s;

@@ -211,4 +211,112 @@ __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const P
   }
 }
 
+// ---- per-line form of the refinement residual (specialised kernels) --------------------------
+// Everything that depends only on the line (neighbour line pointers, double-float stencil
+// coefficients, the split mean of f) is set up once per line.  The stencil sum is accumulated
+// in the compensated "Dot2" form (Ogita, Rump and Oishi, 2005): each product coef * d is split
+// exactly into p + pi by an FMA, the p are summed with TwoSum and all error terms go into one
+// correction, giving the result as if computed with twice the FP32 precision.
+struct ResidLine {
+  const float *P, *Pzm, *Pzp, *Pym, *Pyp;   // pressure hi: this line, z-1, z+1, y-1, y+1
+  const float *Q, *Qzm, *Qzp, *Qym, *Qyp;   // pressure lo (Q null when absent)
+  const double* f;
+  df cx, cz, ca, cc;
+  float mh, ml;
+  int nx;
+};
+
+template <typename TT>
+__device__ __forceinline__ ResidLine resid_line(const Geometry& g, const FwdArgs& args, const TT& tt,
+                                                const DevTables& tb, int line, float mh, float ml) {
+  const int j = line / g.nz, k = line - j * g.nz;
+  const size_t nx = g.nx, plane = (size_t)g.nz * nx;
+  const size_t row = (size_t)line * nx;
+  const size_t rkm = ((size_t)j * g.nz + (k == 0 ? g.nz - 1 : k - 1)) * nx;
+  const size_t rkp = ((size_t)j * g.nz + (k + 1 == g.nz ? 0 : k + 1)) * nx;
+  const float* P = reinterpret_cast<const float*>(args.p);
+  const float* Q = reinterpret_cast<const float*>(args.plo);
+  ResidLine R;
+  R.P = P + row; R.Pzm = P + rkm; R.Pzp = P + rkp;
+  R.Pym = j >= 1 ? P + row - plane : nullptr;
+  R.Pyp = j + 1 <= g.ny - 1 ? P + row + plane : nullptr;
+  R.Q = Q ? Q + row : nullptr;
+  R.Qzm = Q ? Q + rkm : nullptr; R.Qzp = Q ? Q + rkp : nullptr;
+  R.Qym = (Q && R.Pym) ? Q + row - plane : nullptr;
+  R.Qyp = (Q && R.Pyp) ? Q + row + plane : nullptr;
+  R.f = reinterpret_cast<const double*>(args.in) + row;
+  R.cx = df{args.idx2h, args.idx2l};
+  R.cz = df{args.idz2h, args.idz2l};
+  R.ca = df{tt.a[j], tt.a_lo[j]};
+  R.cc = df{tt.c[j], tt.c_lo[j]};
+  R.mh = mh;
+  R.ml = ml;
+  R.nx = g.nx;
+  return R;
+}
+
+// (S, C) -= coef * (d.hi + d.lo), compensated.
+__device__ __forceinline__ void dot2_sub(float& S, float& C, df coef, df d) {
+  const float p = coef.hi * d.hi;
+  float q = fmaf(coef.hi, d.hi, -p);
+  q = fmaf(coef.lo, d.hi, q);
+  q = fmaf(coef.hi, d.lo, q);
+  const df s = two_sum_df(S, -p);
+  S = s.hi;
+  C += s.lo - q;
+}
+
+__device__ __forceinline__ float2 ld_f2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+__device__ __forceinline__ float2 resid_pair_line(const ResidLine& R, int n) {
+  const int i0 = 2 * n;
+  const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
+  const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
+  const float2 pc = ld_f2(R.P + i0);
+  const float pm = R.P[im], pp = R.P[ip];
+  const float2 zm = ld_f2(R.Pzm + i0), zp = ld_f2(R.Pzp + i0);
+  const float2 ym = R.Pym ? ld_f2(R.Pym + i0) : make_float2(0.f, 0.f);
+  const float2 yp = R.Pyp ? ld_f2(R.Pyp + i0) : make_float2(0.f, 0.f);
+  const double2 fv = *reinterpret_cast<const double2*>(R.f + i0);
+  float2 qc = make_float2(0.f, 0.f), qzm = qc, qzp = qc, qym = qc, qyp = qc;
+  float qm = 0.f, qp = 0.f;
+  if (R.Q) {
+    qc = ld_f2(R.Q + i0);
+    qm = R.Q[im];
+    qp = R.Q[ip];
+    qzm = ld_f2(R.Qzm + i0);
+    qzp = ld_f2(R.Qzp + i0);
+    if (R.Qym) qym = ld_f2(R.Qym + i0);
+    if (R.Qyp) qyp = ld_f2(R.Qyp + i0);
+  }
+  float out[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float ctr = c ? pc.y : pc.x;
+    const float xl = c ? pc.x : pm, xr = c ? pp : pc.y;
+    float fh, fl;
+    f64_split(c ? fv.y : fv.x, fh, fl);
+    const df s0 = two_sum_df(fh, -R.mh);
+    float S = s0.hi, C = s0.lo + (fl - R.ml);
+    dot2_sub(S, C, R.cx, two_diff_df(xr, ctr));
+    dot2_sub(S, C, R.cx, two_diff_df(xl, ctr));
+    dot2_sub(S, C, R.cz, two_diff_df(c ? zp.y : zp.x, ctr));
+    dot2_sub(S, C, R.cz, two_diff_df(c ? zm.y : zm.x, ctr));
+    if (R.Pym) dot2_sub(S, C, R.ca, two_diff_df(c ? ym.y : ym.x, ctr));
+    if (R.Pyp) dot2_sub(S, C, R.cc, two_diff_df(c ? yp.y : yp.x, ctr));
+    if (R.Q) {
+      const float qctr = c ? qc.y : qc.x;
+      const float qxl = c ? qc.x : qm, qxr = c ? qp : qc.y;
+      dot2_sub(S, C, R.cx, two_diff_df(qxr, qctr));
+      dot2_sub(S, C, R.cx, two_diff_df(qxl, qctr));
+      dot2_sub(S, C, R.cz, two_diff_df(c ? qzp.y : qzp.x, qctr));
+      dot2_sub(S, C, R.cz, two_diff_df(c ? qzm.y : qzm.x, qctr));
+      if (R.Qym) dot2_sub(S, C, R.ca, two_diff_df(c ? qym.y : qym.x, qctr));
+      if (R.Qyp) dot2_sub(S, C, R.cc, two_diff_df(c ? qyp.y : qyp.x, qctr));
+    }
+    out[c] = S + C;
+  }
+  return make_float2(out[0], out[1]);
+}
+
 }  // namespace pp
