@@ -98,6 +98,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------------- ranks
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (identity without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, points_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job Gpts/s of N independent replicas timed by the slowest rank."""
+    return world * points_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------------------- roofline model
 def kernel_model(name: str, nx: int, ny: int, nz: int):
     """Algorithmic HBM bytes and FFT flops of one launch of each FP64 projection kernel.
@@ -239,12 +257,8 @@ def run_gpu(args):
     barrier()
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * CASE.npoints / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_total / args.steps, dev)
+    value = replica_throughput(world, CASE.npoints, ms_step)
 
     # dominant kernel and its roofline
     totals = {k: sum(vs) for k, vs in stage.items()}
@@ -281,11 +295,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         plan.project_host(uh, vh, wh, DT, staging, p_h=ph)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     h2d = 8 * (3 * CASE.npoints + CASE.nx * CASE.nz)
     d2h = h2d + 8 * CASE.npoints
 
@@ -356,6 +366,44 @@ def precision_forms(dev, steps: int = 5, warmup: int = 3):
     return out
 
 
+PROFILE_CASES = {
+    # name: (case, precision, refine_steps, projection)
+    "fp64_projection_256": (W.CHANNEL_256, 0, 0, True),
+    "fp64_projection_512": (W.CHANNEL_512, 0, 0, True),
+    "fp32_solve_512": (W.CHANNEL_512, 1, 0, False),
+    "fp32_refined_solve_512": (W.CHANNEL_512, 2, 1, False),
+}
+
+
+def profile_case(name: str, repeats: int = 2):
+    """Run a named case `repeats` times without timing (for ncu captures of single kernels)."""
+    import torch
+    from paper_2104_08863_gb300 import build as b
+    b.build()
+    import paper_2104_08863_gb300 as P
+    case, prec, steps, proj = PROFILE_CASES[name]
+    dev = torch.device("cuda", 0)
+    faces = W.tanh_faces(case.ny, case.stretch)
+    plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=PDD_PARTS
+                  if case.ny % PDD_PARTS == 0 else 0, refine_steps=max(steps, 1), device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    dtype = torch.float32 if prec == P.PP_FP32 else torch.float64
+    if proj:
+        u = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        v = torch.randn(case.ny + 1, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        w = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        for _ in range(repeats):
+            plan.project(u, v, w, DT)
+    else:
+        f = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        p = torch.empty_like(f)
+        for _ in range(repeats):
+            plan.solve(f, out=p)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_case": name, "launches_per_call": plan.last_launch_count}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,10 +413,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 1536x768x1024 precision-form comparison")
     ap.add_argument("--forms-only", action="store_true")
+    ap.add_argument("--profile", choices=sorted(PROFILE_CASES), help="run a named case for ncu, no timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile:
+        profile_case(args.profile)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.forms_only:
         import torch

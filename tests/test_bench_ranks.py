@@ -1,0 +1,41 @@
+"""The multi-rank path of bench.py (replicas, max-over-ranks timing) with two gloo ranks on CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = 10.0 + 5.0 * rank              # rank 1 is the slowest
+    m = bench.max_over_ranks(ms)
+    out[rank] = (m, bench.replica_throughput(world, 1_000_000, m))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_replica_throughput_two_gloo_ranks():
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0
+    # two replicas of 1e6 points each, timed by the slower rank (15 ms)
+    assert abs(res[0][1] - 2 * 1e6 / 15e-3 / 1e9) < 1e-12
+
+
+def test_single_process_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
