@@ -148,6 +148,12 @@ def measured_peaks():
         return {}
 
 
+# DRAM bytes (read + write) of one fwd_x launch, from an ncu capture of the same kernel on the
+# 256x192x256 projection, scaled by the number of points (x 8.0) to the 512x384x512 launch; the
+# capture also shows the FP64 pipe 86 % busy.  Valid for the kernel as captured.
+FWD_X_FP64_TRAFFIC = {"bytes": 3.05e9, "ncu_fp64_pipe_active_pct": 85.9,
+                      "source": "ncu capture at 256x192x256 scaled x8 by points"}
+
 # FP64 FMA throughput measured on this machine's GB300 by a DFMA-throughput microbenchmark:
 # 502 G DFMA/s (1.6 per clock per SM at the 2070 MHz nominal clock) = 1004 GFLOP/s.
 FP64_PEAK_GFLOPS = 1004.0
@@ -272,8 +278,11 @@ def run_gpu(args):
     t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
     if t_alu > t_hbm:
         achieved = flops / (avg_ms * 1e-3) / 1e12
+        tr = FWD_X_FP64_TRAFFIC if dom == "fwd_x" else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None, "kernel": dom,
+                "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": tr["bytes"] if tr else None,
+                "traffic_source": tr["source"] if tr else None,
+                "ncu_fp64_pipe_active_pct": tr["ncu_fp64_pipe_active_pct"] if tr else None, "kernel": dom,
                 "peak_source": "measured FP64 DFMA throughput (2 flops/DFMA)",
                 "hbm_achieved_gbs": nbytes / (avg_ms * 1e-3) / 1e9}
     else:
