@@ -375,6 +375,61 @@ def precision_forms(dev, steps: int = 5, warmup: int = 3):
     return out
 
 
+def batch_form(dev, steps: int = 5, warmup: int = 2, tune: bool = True):
+    """64 uneven FP32 solves (default_rng(5) sizes): sequential plain solves vs one batched graph launch.
+
+    Right-hand sides: seeded N(0, 1) fields drawn on the device.  Reports aggregate Gpts/s of
+    both, the batch's kernel launches replayed per graph launch, and the autotuner's choices.
+    """
+    import torch
+    import paper_2104_08863_gb300 as P
+    cases = W.batch_instances(5, 64)
+    total = sum(c.npoints for c in cases)
+    specs = [dict(nx=c.nx, ny=c.ny, nz=c.nz, y_faces=W.tanh_faces(c.ny, c.stretch)) for c in cases]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    rhs = [torch.randn(c.ny, c.nz, c.nx, dtype=torch.float32, device=dev, generator=gen) for c in cases]
+    outs = [torch.empty_like(r) for r in rhs]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    plans = [P.Plan(c.nx, c.ny, c.nz, sp["y_faces"], precision=P.PP_FP32, device=dev) for c, sp in zip(cases, specs)]
+    ms_seq = timed(lambda: [pl.solve(r, out=o) for pl, r, o in zip(plans, rhs, outs)])
+    del plans
+    bp = P.BatchPlan(specs, precision=P.PP_FP32, device=dev)
+    ms_batch = timed(lambda: bp.solve(rhs, out=outs))
+    out = {"workload": "64 uneven FP32 Poisson solves, sizes from default_rng(5)", "points": total,
+           "sequential_ms": ms_seq, "sequential_gpts_s": total / (ms_seq * 1e-3) / 1e9,
+           "batched_graph_ms": ms_batch, "batched_graph_gpts_s": total / (ms_batch * 1e-3) / 1e9,
+           "kernels_per_graph_launch": bp.last_launch_count}
+    del bp
+    if tune:
+        t0 = time.perf_counter()
+        bt, strat = P.tune_batch(specs, precision=P.PP_FP32, device=dev)
+        tune_s = time.perf_counter() - t0
+        ms_tuned = timed(lambda: bt.solve(rhs, out=outs))
+        best = min(strat, key=strat.get)
+        out.update({"batched_tuned_ms": ms_tuned, "batched_tuned_gpts_s": total / (ms_tuned * 1e-3) / 1e9,
+                    "autotune_s": tune_s, "autotune_strategy": best,
+                    "autotune_strategy_ms": {k: round(v, 4) for k, v in strat.items()},
+                    "tuned_parts_hist": {str(k): sum(1 for t in bt.tuned if t[0] == k)
+                                         for k in sorted(set(t[0] for t in bt.tuned))}})
+        del bt
+    torch.cuda.empty_cache()
+    return out
+
+
 PROFILE_CASES = {
     # name: (case, precision, refine_steps, projection)
     "fp64_projection_256": (W.CHANNEL_256, 0, 0, True),
@@ -422,6 +477,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the 1536x768x1024 precision-form comparison")
     ap.add_argument("--forms-only", action="store_true")
+    ap.add_argument("--batch-only", action="store_true", help="only the 64-instance batched form")
     ap.add_argument("--profile", choices=sorted(PROFILE_CASES), help="run a named case for ncu, no timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -430,6 +486,11 @@ def main():
         profile_case(args.profile)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.batch_only:
+        import torch
+        from paper_2104_08863_gb300 import build as b
+        b.build()
+        print(json.dumps(batch_form(torch.device("cuda", 0))))
     elif args.forms_only:
         import torch
         from paper_2104_08863_gb300 import build as b

@@ -62,6 +62,8 @@ typedef enum {
 
 #define POISSON_CHECK_FINITE 0x1u   /* flag: scan inputs, set PS_ENONFINITE on NaN/Inf     */
 #define POISSON_TIMING       0x2u   /* flag: record CUDA events around every kernel launch */
+#define POISSON_GENERIC_FFT  0x4u   /* flag: use the runtime-generic FFT kernels instead of the
+                                       compile-time specialised ones (a tiling the autotuner tries) */
 
 typedef struct {
   int nx, ny, nz;           /* cells; nx even, nx/2 and nz of the form 2^a 3^b; ny >= 2 */
@@ -133,6 +135,28 @@ poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_h
  * per device, so calls that overlap on the GPU (different streams, threads or plans) race:
  * serialise them. */
 poisson_status poisson_solve_static_ws(poisson_plan_t plan, const void* rhs, void* p, void* stream);
+
+/* Batched form: `count` independent solves of possibly different sizes and precisions
+ * (descs[i] as for poisson_plan_create).  poisson_workspace_size reports the sum of the
+ * instances' workspaces and poisson_set_workspace carves one caller allocation.  The batch
+ * is solved by poisson_solve_batched only (poisson_solve on it returns PS_EINVAL). */
+poisson_status poisson_plan_batched(const poisson_desc* descs, int count, poisson_plan_t* out);
+
+/* Solve every instance i of a batched plan: rhs[i] -> p[i] (host arrays of `count` device
+ * pointers, laid out and typed as for poisson_solve).  All instances run in ONE CUDA graph
+ * launch on `stream`: each instance's kernel sequence is a branch of the graph, so kernels of
+ * different instances run concurrently.  The graph is captured on the first call and replayed
+ * while the pointer arrays stay the same (a change of pointers re-captures it).  The first
+ * call also runs the batch once outside capture; make it before capturing `stream` yourself. */
+poisson_status poisson_solve_batched(poisson_plan_t plan, const void* const* rhs, void* const* p, void* stream);
+
+/* Autotuner: for the grid of `desc`, time poisson_solve with every candidate PDD partition
+ * count (1 and the divisors P of ny with 2 <= P <= 32 and ny/P >= 4) and both FFT tilings
+ * (specialised, generic) on `stream`, and return the fastest in *pdd_parts and *flags (the
+ * POISSON_GENERIC_FFT bit) with its time in *ms.  It allocates and frees its own device buffers
+ * (set-up time, not the solve path) and synchronises `stream`. */
+poisson_status poisson_autotune(const poisson_desc* desc, void* stream, int* pdd_parts, unsigned* flags,
+                                float* ms);
 
 /* Synchronise `stream` and read the device status word (PS_OK, PS_ENONFINITE, ...),
  * then clear it. */

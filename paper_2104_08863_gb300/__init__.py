@@ -14,9 +14,9 @@ import torch
 
 from . import _native
 from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_PDD_EXACT,
-                      POISSON_CHECK_FINITE, POISSON_TIMING, PoissonError, check)
+                      POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, PoissonError, check)
 
-__all__ = ["Plan", "ProjectionFn", "PoissonError", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
+__all__ = ["Plan", "BatchPlan", "autotune", "tune_batch", "ProjectionFn", "PoissonError", "POISSON_GENERIC_FFT", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
            "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "POISSON_CHECK_FINITE", "POISSON_TIMING"]
 
 
@@ -133,6 +133,142 @@ class Plan:
         if h is not None and _native._LIB is not None:
             _native._LIB.poisson_plan_destroy(h)
             self._h = None
+
+
+def _desc(nx, ny, nz, faces, lx, lz, precision, tridiag, pdd_parts, fp64_low_modes, refine_steps, flags):
+    faces = np.ascontiguousarray(np.asarray(faces, dtype=np.float64))
+    d = _native.PoissonDesc(int(nx), int(ny), int(nz), float(lx), float(lz),
+                            faces.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(precision), int(tridiag),
+                            int(pdd_parts), int(fp64_low_modes), int(refine_steps), int(flags))
+    return d, faces
+
+
+def autotune(nx, ny, nz, y_faces, lx=2 * np.pi, lz=np.pi, precision=PP_FP32, fp64_low_modes=4, refine_steps=1,
+             stream=None):
+    """Time every PDD partition count and both FFT tilings on the device; returns (parts, flags, ms)."""
+    d, _keep = _desc(nx, ny, nz, y_faces, lx, lz, precision, PT_PDD_EXACT, 0, fp64_low_modes, refine_steps, 0)
+    parts, flags, ms = ctypes.c_int(), ctypes.c_uint(), ctypes.c_float()
+    check(_native.lib().poisson_autotune(ctypes.byref(d), _stream(stream), ctypes.byref(parts), ctypes.byref(flags),
+                                         ctypes.byref(ms)), "poisson_autotune")
+    return int(parts.value), int(flags.value), float(ms.value)
+
+
+class BatchPlan:
+    """Independent solves of uneven sizes run as one graph launch (poisson_solve_batched).
+
+    specs: sequence of dicts with keys nx, ny, nz, y_faces (and optional lx, lz, pdd_parts,
+    flags).  With tune=True each distinct grid is autotuned once (partition count, FFT tiling).
+    """
+
+    def __init__(self, specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, tune=False, device=None):
+        L = _native.lib()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.precision = int(precision)
+        self.specs = [dict(s) for s in specs]
+        cache = {}
+        descs = (_native.PoissonDesc * len(self.specs))()
+        self._keep = []
+        self.tuned = []
+        for i, s in enumerate(self.specs):
+            lx, lz = s.get("lx", 2 * np.pi), s.get("lz", np.pi)
+            parts, flags = s.get("pdd_parts", 0), s.get("flags", 0)
+            if tune:
+                key = (s["nx"], s["ny"], s["nz"], tuple(np.round(np.asarray(s["y_faces"]), 12)))
+                if key not in cache:
+                    cache[key] = autotune(s["nx"], s["ny"], s["nz"], s["y_faces"], lx, lz, precision, fp64_low_modes,
+                                          refine_steps)
+                parts, flags, _ = cache[key]
+            self.tuned.append((parts, flags))
+            tri = PT_THOMAS if parts == 1 else (PT_PDD_EXACT if parts > 1 else PT_AUTO)
+            d, faces = _desc(s["nx"], s["ny"], s["nz"], s["y_faces"], lx, lz, precision, tri, parts, fp64_low_modes,
+                             refine_steps, flags)
+            descs[i] = d
+            self._keep.append(faces)
+        h = ctypes.c_void_p()
+        check(L.poisson_plan_batched(descs, len(self.specs), ctypes.byref(h)), "poisson_plan_batched")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        check(L.poisson_workspace_size(h, ctypes.byref(nbytes)), "poisson_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-self._ws.data_ptr()) % 256
+            check(L.poisson_set_workspace(h, self._ws.data_ptr() + off, self.workspace_bytes, _stream()),
+                  "poisson_set_workspace")
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.precision == PP_FP32 else torch.float64
+
+    def solve(self, rhs, out=None, stream=None):
+        n = len(self.specs)
+        if len(rhs) != n:
+            raise ValueError(f"expected {n} right-hand sides")
+        out = [torch.empty_like(r) for r in rhs] if out is None else out
+        for s, r, o in zip(self.specs, rhs, out):
+            shape = (s["ny"], s["nz"], s["nx"])
+            for t in (r, o):
+                if t.dtype != self.dtype or tuple(t.shape) != shape or not t.is_contiguous() or not t.is_cuda:
+                    raise ValueError(f"expected contiguous CUDA {self.dtype} {shape}")
+        pr = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhs])
+        po = (ctypes.c_void_p * n)(*[o.data_ptr() for o in out])
+        check(_native.lib().poisson_solve_batched(self._h, pr, po, _stream(stream)), "poisson_solve_batched")
+        return out
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(_native.lib().poisson_last_launch_count(self._h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _native._LIB is not None:
+            _native._LIB.poisson_plan_destroy(h)
+            self._h = None
+
+
+def _max_parts(ny):
+    best = 1
+    for P in range(2, 33):
+        if ny % P == 0 and ny // P >= 4:
+            best = P
+    return best
+
+
+def tune_batch(specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, device=None, repeats=3):
+    """Batch-level autotuner: time whole batched graph launches for several partition strategies
+    (the plan's model, per-shape autotuning, Thomas everywhere, the largest partition count) on
+    the device and return (best BatchPlan, {strategy: ms})."""
+    dev = torch.device(device if device is not None else "cuda")
+    dtype = torch.float32 if precision == PP_FP32 else torch.float64
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    rhs = [torch.randn(s["ny"], s["nz"], s["nx"], dtype=dtype, device=dev, generator=gen) for s in specs]
+    outs = [torch.empty_like(r) for r in rhs]
+    strategies = {
+        "model": [dict(s) for s in specs],
+        "thomas": [dict(s, pdd_parts=1) for s in specs],
+        "max_parts": [dict(s, pdd_parts=_max_parts(s["ny"])) for s in specs],
+    }
+    times, best, best_ms = {}, None, None
+    for name in ("model", "per_shape", "thomas", "max_parts"):
+        bp = BatchPlan(specs if name == "per_shape" else strategies[name], precision, fp64_low_modes, refine_steps,
+                       tune=(name == "per_shape"), device=dev)
+        bp.solve(rhs, out=outs)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(repeats):
+            bp.solve(rhs, out=outs)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / repeats
+        times[name] = ms
+        if best_ms is None or ms < best_ms:
+            best, best_ms = bp, ms
+        else:
+            del bp
+    best.strategy_times = times
+    return best, times
 
 
 class ProjectionFn(torch.autograd.Function):

@@ -18,11 +18,13 @@ PT_AUTO, PT_THOMAS, PT_PDD_EXACT = 0, 1, 2
 POISSON_STATIC_WS_MAX_BYTES = 8 * 1024 * 1024
 POISSON_CHECK_FINITE = 0x1
 POISSON_TIMING = 0x2
+POISSON_GENERIC_FFT = 0x4
 
 # Every symbol declared in include/poisson.h.
 EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
-    "poisson_solve_static_ws", "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
+    "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
+    "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
     "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
@@ -61,6 +63,10 @@ def lib() -> ctypes.CDLL:
     L.poisson_set_workspace.argtypes = [vp, vp, sz, vp]
     L.poisson_solve.argtypes = [vp, vp, vp, vp]
     L.poisson_solve_static_ws.argtypes = [vp, vp, vp, vp]
+    L.poisson_plan_batched.argtypes = [ctypes.POINTER(PoissonDesc), i, ctypes.POINTER(vp)]
+    L.poisson_solve_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.poisson_autotune.argtypes = [ctypes.POINTER(PoissonDesc), vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_uint),
+                                   ctypes.POINTER(ctypes.c_float)]
     L.projection_step.argtypes = [vp, vp, vp, vp, vp, d, vp]
     L.projection_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
     L.projection_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, vp]
@@ -73,7 +79,7 @@ def lib() -> ctypes.CDLL:
     L.poisson_status_string.argtypes = [i]
     L.poisson_status_string.restype = ctypes.c_char_p
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
-                 "poisson_solve_static_ws",
+                 "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
                  "projection_step", "projection_step_adjoint", "projection_step_host",
                  "poisson_device_status", "poisson_plan_destroy"):
         getattr(L, name).restype = i

@@ -10,7 +10,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -63,6 +65,18 @@ bool spec_is_fp64(const poisson_plan_s* pl) { return pl->precision == PP_FP64; }
 }  // namespace
 
 namespace pp {
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> granted;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = granted.find(kernel);
+  if (it != granted.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted[kernel] = bytes;
+  return e;
+}
+
 DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
   DevTables dt;
   unsigned char* tb = base + pl->off_tables;
@@ -151,6 +165,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   g.pitch = (g.ncols + cpad - 1) / cpad * cpad;
   g.dx = d->lx / d->nx;
   g.dz = d->lz / d->nz;
+  g.generic_fft = (d->flags & POISSON_GENERIC_FFT) ? 1 : 0;
   pl->lx = d->lx; pl->lz = d->lz;
   pl->precision = d->precision;
   pl->tridiag = d->tridiag;
@@ -286,13 +301,14 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
 
 poisson_status poisson_workspace_size(poisson_plan_t pl, size_t* bytes) {
   if (!pl || !bytes) return PS_EINVAL;
-  *bytes = pl->ws_bytes;
+  *bytes = pl->ws_bytes;   // batched plans: the sum of their sub-plans' aligned workspaces
   return PS_OK;
 }
 
 poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, void* stream) {
   if (!pl || !ws) return PS_EINVAL;
   if (bytes < pl->ws_bytes || ((uintptr_t)ws & 255u)) return PS_EINVAL;
+  if (!pl->children.empty()) return pp::set_batch_workspace(pl, (unsigned char*)ws, stream);
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* base = (unsigned char*)ws;
   cudaError_t e = cudaMemcpyAsync(base + pl->off_tables, pl->host_tables.data(), pl->host_tables.size(),
@@ -492,6 +508,7 @@ extern "C" {
 
 poisson_status poisson_solve(poisson_plan_t pl, const void* rhs, void* p, void* stream) {
   if (!pl || !rhs || !p) return PS_EINVAL;
+  if (!pl->children.empty()) return PS_EINVAL;   // batched plans use poisson_solve_batched
   if (!pl->ws) return PS_ENOWORKSPACE;
   if (!aligned16(rhs) || !aligned16(p)) return PS_EINVAL;
   if (pl->precision == PP_FP32_REFINED && rhs == p) return PS_EINVAL;  // the residual re-reads rhs
@@ -608,8 +625,10 @@ int poisson_stage_times(poisson_plan_t pl, float* ms, const char** names, int ma
 }
 
 poisson_status poisson_plan_destroy(poisson_plan_t pl) {
-  if (pl)
+  if (pl) {
     for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+    pp::destroy_batch(pl);
+  }
   delete pl;
   return PS_OK;
 }

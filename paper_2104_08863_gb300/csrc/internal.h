@@ -51,11 +51,16 @@ struct DevTables {
 struct Geometry {
   int nx, ny, nz, M, ncols, pitch;
   double dx, dz;
+  int generic_fft;   // 1: use the runtime-generic FFT kernels (POISSON_GENERIC_FFT)
 };
 
 struct LaunchCount {
   int n = 0;
 };
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, once per kernel (a registry
+// keyed by the kernel's address), so that the attribute call does not recur inside stream capture.
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes);
 
 // --- launchers (return cudaGetLastError() after the launch) --------------------------
 enum FwdMode { FWD_PLAIN = 0, FWD_DIV = 1, FWD_RESID = 2, FWD_GRADT = 3 };
@@ -177,6 +182,14 @@ struct poisson_plan_s {
   std::vector<cudaEvent_t> ev;
   std::vector<const char*> ev_names;
   int nev;
+  // batched plans (poisson_plan_batched): sub-plans, fork streams and the cached graph
+  std::vector<poisson_plan_s*> children;
+  std::vector<cudaStream_t> forks;
+  std::vector<cudaEvent_t> fork_ev;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> g_rhs;
+  std::vector<void*> g_p;
+  bool warmed = false;
 };
 
 namespace pp {
@@ -185,4 +198,7 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base);
 // poisson_solve's pipeline on an explicit workspace (no timing events).
 poisson_status solve_on_workspace(poisson_plan_s* pl, unsigned char* ws, const DevTables& dt, const void* rhs,
                                   void* p, cudaStream_t st);
+// Batched plans (csrc/batch.cu).
+poisson_status set_batch_workspace(poisson_plan_s* pl, unsigned char* ws, void* stream);
+void destroy_batch(poisson_plan_s* pl);
 }  // namespace pp

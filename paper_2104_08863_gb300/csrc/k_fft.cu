@@ -137,14 +137,13 @@ template <> const Tables<float>& tabs<float>(const DevTables& tb) { return tb.f;
 
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaSuccess;
+  return ensure_smem_limit((const void*)kernel, smem);
 }
 
 template <typename T, typename TI>
 cudaError_t launch_fwd_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, FwdMode mode,
                          const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
-  {
+  if (!g.generic_fft) {
     cudaError_t ef;
     if constexpr (sizeof(T) == 8) ef = launch_fwd_x_fast_dd(g, tb, mode, args, (cplx<double>*)spec, st);
     else if constexpr (sizeof(TI) == 4) ef = launch_fwd_x_fast_ff(g, tb, mode, args, (cplx<float>*)spec, st);
@@ -176,7 +175,7 @@ template <typename T, typename TO>
 cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactors& fm, InvMode mode,
                          const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
                          PairArgs pair) {
-  {
+  if (!g.generic_fft) {
     cudaError_t ef;
     if constexpr (sizeof(T) == 8)
       ef = launch_inv_x_fast_dd(g, tb, mode, (const cplx<double>*)spec, (double*)out, scale, accumulate, st, pair);
@@ -215,7 +214,7 @@ cudaError_t launch_inv_x(const Geometry& g, const DevTables& tb, const FftFactor
 template <typename T>
 cudaError_t launch_fft_z(const Geometry& g, const DevTables& tb, const FftFactors& fz, int sign, cplx<T>* spec,
                          cudaStream_t st) {
-  {
+  if (!g.generic_fft) {
     const cudaError_t ef = launch_fft_z_fast<T>(g, tabs<T>(tb), sign, spec, st);
     if (ef != cudaErrorNotSupported) return ef;
   }

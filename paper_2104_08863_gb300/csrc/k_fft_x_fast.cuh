@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, int smem) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return ensure_smem_limit((const void*)kernel, (size_t)smem);
 }
 
 template <typename T, typename TI, int M>

@@ -45,6 +45,11 @@ __global__ void __launch_bounds__(ZTile<T, NZ>::THREADS, ZTile<T, NZ>::MINB) k_f
   }
 }
 
+template <typename K>
+static cudaError_t set_smem_once(K kernel, int smem) {
+  return ensure_smem_limit((const void*)kernel, (size_t)smem);
+}
+
 template <typename T, int NZ>
 static cudaError_t launch_z(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st) {
   using C = ZTile<T, NZ>;
@@ -52,11 +57,11 @@ static cudaError_t launch_z(const Geometry& g, const Tables<T>& tt, int sign, cp
   cudaError_t e;
   if (sign < 0) {
     auto k = k_fft_z_fast<T, NZ, -1>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
     k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
   } else {
     auto k = k_fft_z_fast<T, NZ, 1>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
     k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
   }
   return cudaGetLastError();

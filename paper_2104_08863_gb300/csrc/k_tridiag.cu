@@ -496,8 +496,7 @@ __global__ void __launch_bounds__(32) k_mode00(Geometry g, const double* __restr
 // ------------------------------------------------------------------------------ launchers
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaSuccess;
+  return ensure_smem_limit((const void*)kernel, smem);
 }
 
 template <typename TC> static const TC* coef_a(const DevTables& tb);

@@ -116,3 +116,21 @@ def manufactured_rhs(nx: int, ny: int, nz: int, faces: np.ndarray,
             * np.cos(4.0 * np.pi * z / lz)[None, :, None]
             * np.cos(2.0 * np.pi * x / lx)[None, None, :])
 
+
+
+BATCH_NX_NZ = (64, 96, 128, 192, 256, 384)
+BATCH_NY = (48, 64, 96, 128, 192)
+
+
+def batch_instances(seed: int = 5, count: int = 64):
+    """Uneven-size batch: per instance, in order, Nx and Nz from BATCH_NX_NZ, Ny from BATCH_NY and
+    the tanh stretching from U(1.0, 2.5), all drawn from one default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nx = int(rng.choice(BATCH_NX_NZ))
+        nz = int(rng.choice(BATCH_NX_NZ))
+        ny = int(rng.choice(BATCH_NY))
+        s = float(rng.uniform(1.0, 2.5))
+        out.append(ChannelCase(f"batch_{nx}x{ny}x{nz}_tanh{s:.3f}", nx, ny, nz, s))
+    return out
