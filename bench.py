@@ -1,15 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark of the pressure-projection hot path on GB300.
+"""Benchmark of the fully explicit projection timestep on GB300.
 
-One step = one projection (Eqs. 4 and 7): the divergence of u* fused into the forward x-FFT,
-the forward z-FFT, the PDD wall-normal solves (P = 8, exact reduced system), the (0, 0) mode,
-the inverse z- and x-FFTs, and the gradient correction, in FP64, on the 512 x 384 x 512
-channel (Lx = 2 pi, Ly = 2, Lz = pi, tanh stretching 2.0).  Input: laminar Poiseuille profile
-plus seeded N(0, 0.1^2) noise (seed 1), no-penetration walls, dt = 1e-4.
+One step = one full FP64 timestep (Sec. 2, Eqs. 3-7) on the 512 x 384 x 512 channel (Lx = 2 pi,
+Ly = 2, Lz = pi, tanh stretching 2.0): the two stages of Heun's RK2 momentum predictor (central
+advection and diffusion, nu = 1/550, body force 2 nu), then the projection: the divergence of u*
+fused into the forward x-FFT, the forward z-FFT, the PDD wall-normal solves (P = 8, exact
+reduced system), the (0, 0) mode, the inverse z- and x-FFTs, and the gradient correction.
+Input: laminar Poiseuille profile plus seeded N(0, 0.1^2) noise (seed 1), no-penetration walls,
+dt = 1e-4.
 
-Metric: Poisson-solve throughput in Gpts/s (grid points per second of whole projection steps).
-The fields (2.4 GB of velocity, 0.8 GB spectrum) are far larger than the 129 MB L2, so no flush
-is needed between steps.
+Metric: grid points per second of whole timesteps (Gpts/s) and ms/timestep; the Poisson solve's
+own throughput (the projection's kernels) is reported beside it.  The fields (2.4 GB of velocity,
+2.4 GB of stage scratch, 0.8 GB spectrum) are far larger than the 129 MB L2, so no flush is
+needed between steps.
 
 --impl reference times the CPU oracle (numpy, FP64) on a bounded sample of the same workload.
 Under torchrun every rank runs an independent replica (the path is replicas-only on this pool).
@@ -37,7 +40,10 @@ import workloads as W  # noqa: E402
 CASE = W.CHANNEL_512
 PDD_PARTS = 8
 DT = 1e-4
-METRIC = "Poisson solve Gpts/s (FP64 projection step: divergence + FFT/PDD solve + gradient)"
+NU = 1.0 / 550.0
+FX = 2.0 * NU      # body force that keeps u = 1 - y^2 steady in the continuum
+METRIC = ("Poisson solve Gpts/s & ms/timestep (FP64 full timestep: RK2 momentum predictor + "
+          "projection = divergence + FFT/PDD solve + gradient)")
 UNIT = "Gpts/s"
 
 
@@ -137,7 +143,19 @@ def kernel_model(name: str, nx: int, ny: int, nz: int):
         return 16 * Ns + 8 * N, 2.5 * N * math.log2(nx)
     if name == "gradient":     # read p, u, v, w; write u, v, w
         return 8 * N + 2 * 8 * (3 * N + plane), 0.0
+    if name == "momentum_1":   # read u, v, w; write u_bar; FP64 flops counted per point in the kernel
+        return 2 * 8 * (3 * N + plane), MOMENTUM_FLOPS[0] * N
+    if name == "momentum_2":   # read u_bar (stencil) and u (pointwise); write u_star
+        return 3 * 8 * (3 * N + plane), MOMENTUM_FLOPS[1] * N
     return 0, 0.0
+
+
+# FP64 flops per point of the two momentum stages, counted from k_momentum's arithmetic (an FMA
+# is 2 flops): 20 FMAs + 11 adds/multiplies per component plus the 9 flops of the three shared
+# edge fluxes = 93; stage 2 adds one FMA per component for the base term.  The stages issue 63
+# and 66 FP64 instructions per point.
+MOMENTUM_FLOPS = (93.0, 99.0)
+MOMENTUM_FP64_INSTR = (63.0, 66.0)
 
 
 def measured_peaks():
@@ -154,6 +172,9 @@ def measured_peaks():
 FWD_X_FP64_TRAFFIC = {"bytes": 3.05e9, "ncu_fp64_pipe_active_pct": 85.9,
                       "source": "ncu capture at 256x192x256 scaled x8 by points"}
 
+# DRAM traffic of other kernels from ncu captures (per launch at the bench size), when taken.
+KERNEL_TRAFFIC = {}
+
 # FP64 FMA throughput measured on this machine's GB300 by a DFMA-throughput microbenchmark:
 # 502 G DFMA/s (1.6 per clock per SM at the 2070 MHz nominal clock) = 1004 GFLOP/s.
 FP64_PEAK_GFLOPS = 1004.0
@@ -161,7 +182,7 @@ FP64_PEAK_GFLOPS = 1004.0
 
 # ------------------------------------------------------------------------------- CPU oracle
 def oracle_sample(seconds: float = 12.0):
-    """Time the CPU oracle's projection on a sample of the workload (same Ny, stretching, dt).
+    """Time the CPU oracle's full timestep on a sample of the workload (same Ny, stretching, dt).
 
     The sample keeps the wall-normal grid (Ny = 384, tanh 2.0) and shrinks the periodic plane
     to 64 x 64; the oracle is repeated until about `seconds` have passed.  Returns Gpts/s.
@@ -175,15 +196,16 @@ def oracle_sample(seconds: float = 12.0):
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oracle.project(g, u, v, w, DT)
+        oracle.timestep(g, u, v, w, DT, NU, FX)
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     pts = reps * nx * nz * CASE.ny
     return {"value": pts / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle.project on {nx}x{CASE.ny}x{nz} (same Ny=384 tanh 2.0 wall-normal grid), "
-                      f"{reps} runs in {el:.1f} s, numpy FP64 FFT + extended-precision Thomas, 1 thread"}
+            "sample": f"oracle.timestep (RK2 predictor + projection) on {nx}x{CASE.ny}x{nz} (same Ny=384 "
+                      f"tanh 2.0 wall-normal grid), {reps} runs in {el:.1f} s, numpy FP64 FFT + "
+                      f"extended-precision Thomas, 1 thread"}
 
 
 def run_reference(args):
@@ -209,10 +231,11 @@ def run_reference(args):
 
 
 def config_dict():
-    return {"workload": f"{CASE.name} FP64 projection step", "grid": [CASE.nx, CASE.ny, CASE.nz],
-            "pdd_parts": PDD_PARTS, "tridiag": "PDD, exact reduced system", "dt": DT,
+    return {"workload": f"{CASE.name} FP64 full timestep (RK2 predictor + projection)",
+            "grid": [CASE.nx, CASE.ny, CASE.nz],
+            "pdd_parts": PDD_PARTS, "tridiag": "PDD, exact reduced system", "dt": DT, "nu": NU, "fx": FX,
             "input": "Poiseuille 1-y^2 + N(0,0.1^2) seed 1, walls v=0",
-            "l2": "no flush: fields 2.4 GB >> 129 MB L2", "parallelism": "replicas"}
+            "l2": "no flush: fields 2.4 GB (+2.4 GB stage scratch) >> 129 MB L2", "parallelism": "replicas"}
 
 
 # ------------------------------------------------------------------------------- GPU arm
@@ -242,8 +265,9 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    scratch = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
     for _ in range(args.warmup):
-        plan.project(u, v, w, DT, p_out=p)
+        plan.timestep(u, v, w, DT, NU, FX, p_out=p, scratch=scratch)
     launches_per_step = plan.last_launch_count
     barrier()
     clocks = ClockSampler(torch.cuda.get_device_properties(dev).uuid if hasattr(
@@ -256,7 +280,7 @@ def run_gpu(args):
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        plan.project(u, v, w, DT, p_out=p)
+        plan.timestep(u, v, w, DT, NU, FX, p_out=p, scratch=scratch)
         for name, ms in plan.stage_times():
             stage.setdefault(name, []).append(ms)
     e1.record(stream)
@@ -265,6 +289,12 @@ def run_gpu(args):
     clk = clocks.stop()
     ms_step = max_over_ranks(ms_total / args.steps, dev)
     value = replica_throughput(world, CASE.npoints, ms_step)
+    # the Poisson solve's share: every launch of the projection (all but the momentum stages)
+    proj_ms = sum(sum(vs) for k, vs in stage.items() if not k.startswith("momentum")) / args.steps
+    mom_ms = sum(sum(vs) for k, vs in stage.items() if k.startswith("momentum")) / args.steps
+    poisson = {"gpts": replica_throughput(world, CASE.npoints, max_over_ranks(proj_ms, dev)),
+               "projection_ms": proj_ms, "momentum_ms": mom_ms,
+               "note": "sums of per-launch event times inside the timed steps"}
 
     # dominant kernel and its roofline
     totals = {k: sum(vs) for k, vs in stage.items()}
@@ -278,13 +308,17 @@ def run_gpu(args):
     t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
     if t_alu > t_hbm:
         achieved = flops / (avg_ms * 1e-3) / 1e12
-        tr = FWD_X_FP64_TRAFFIC if dom == "fwd_x" else None
+        tr = FWD_X_FP64_TRAFFIC if dom == "fwd_x" else KERNEL_TRAFFIC.get(dom)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": tr["bytes"] if tr else None,
                 "traffic_source": tr["source"] if tr else None,
                 "ncu_fp64_pipe_active_pct": tr["ncu_fp64_pipe_active_pct"] if tr else None, "kernel": dom,
                 "peak_source": "measured FP64 DFMA throughput (2 flops/DFMA)",
                 "hbm_achieved_gbs": nbytes / (avg_ms * 1e-3) / 1e9}
+        if dom.startswith("momentum"):
+            st_i = int(dom[-1]) - 1
+            roof["fp64_instr_frac"] = (MOMENTUM_FP64_INSTR[st_i] * CASE.npoints / (avg_ms * 1e-3)) / (
+                FP64_PEAK_GFLOPS / 2 * 1e9)
     else:
         achieved = nbytes / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -297,12 +331,12 @@ def run_gpu(args):
     uh, vh, wh = (torch.from_numpy(a).pin_memory() for a in (u0, v0, w0))
     ph = torch.empty(CASE.ny, CASE.nz, CASE.nx, dtype=torch.float64).pin_memory()
     staging = (u, v, w, p)
-    plan.project_host(uh, vh, wh, DT, staging, p_h=ph)
+    plan.timestep_host(uh, vh, wh, DT, NU, FX, staging, scratch, p_h=ph)
     e2e_steps = max(1, min(args.steps, 5))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan.project_host(uh, vh, wh, DT, staging, p_h=ph)
+        plan.timestep_host(uh, vh, wh, DT, NU, FX, staging, scratch, p_h=ph)
     barrier()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     h2d = 8 * (3 * CASE.npoints + CASE.nx * CASE.nz)
@@ -314,7 +348,7 @@ def run_gpu(args):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
-               "roofline": roof, "kernel_share": share,
+               "roofline": roof, "kernel_share": share, "poisson_solve": poisson,
                "cpu_baseline": cpu,
                "e2e": {"value": world * CASE.npoints / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -431,11 +465,13 @@ def batch_form(dev, steps: int = 5, warmup: int = 2, tune: bool = True):
 
 
 PROFILE_CASES = {
-    # name: (case, precision, refine_steps, projection)
-    "fp64_projection_256": (W.CHANNEL_256, 0, 0, True),
-    "fp64_projection_512": (W.CHANNEL_512, 0, 0, True),
-    "fp32_solve_512": (W.CHANNEL_512, 1, 0, False),
-    "fp32_refined_solve_512": (W.CHANNEL_512, 2, 1, False),
+    # name: (case, precision, refine_steps, kind) with kind "timestep", "projection" or "solve"
+    "fp64_timestep_256": (W.CHANNEL_256, 0, 0, "timestep"),
+    "fp64_timestep_512": (W.CHANNEL_512, 0, 0, "timestep"),
+    "fp64_projection_256": (W.CHANNEL_256, 0, 0, "projection"),
+    "fp64_projection_512": (W.CHANNEL_512, 0, 0, "projection"),
+    "fp32_solve_512": (W.CHANNEL_512, 1, 0, "solve"),
+    "fp32_refined_solve_512": (W.CHANNEL_512, 2, 1, "solve"),
 }
 
 
@@ -445,7 +481,7 @@ def profile_case(name: str, repeats: int = 2):
     from paper_2104_08863_gb300 import build as b
     b.build()
     import paper_2104_08863_gb300 as P
-    case, prec, steps, proj = PROFILE_CASES[name]
+    case, prec, steps, kind = PROFILE_CASES[name]
     dev = torch.device("cuda", 0)
     faces = W.tanh_faces(case.ny, case.stretch)
     plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=PDD_PARTS
@@ -453,12 +489,18 @@ def profile_case(name: str, repeats: int = 2):
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     dtype = torch.float32 if prec == P.PP_FP32 else torch.float64
-    if proj:
+    if kind in ("projection", "timestep"):
         u = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
         v = torch.randn(case.ny + 1, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
         w = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        v[0].zero_()
+        v[-1].zero_()
+        scratch = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
         for _ in range(repeats):
-            plan.project(u, v, w, DT)
+            if kind == "timestep":
+                plan.timestep(u, v, w, DT, NU, FX, scratch=scratch)
+            else:
+                plan.project(u, v, w, DT)
     else:
         f = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
         p = torch.empty_like(f)

@@ -117,6 +117,36 @@ poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_h
                                     void* w_host, void* p_host, void* u_dev, void* v_dev,
                                     void* w_dev, void* p_dev, double dt, void* stream);
 
+/* Momentum predictor of the fully explicit projection method (Sec. 2, Eqs. 3, 5, 6): Heun's
+ * RK2 applied in place to u, v, w (same layouts and dtype as projection_step):
+ *   u_bar = u + dt R(u),   u <- u_star = u + dt/2 (R(u) + R(u_bar)),
+ *   R(u) = -div(u u) + nu lap(u) + (fx, 0, 0).
+ * Second-order central differences on the staggered grid: the advection is the divergence form
+ * with two-point face averages (no flux through the walls); the diffusion is the three-point
+ * Laplacian with the no-slip wall value 0 half a cell from the first u and w nodes; fx is a
+ * constant streamwise body force (the mean pressure gradient that drives the channel).  The
+ * wall faces of v are boundary values and are not modified.
+ * ub, vb, wb: caller-owned device scratch of the sizes of u, v, w (they receive u_bar).
+ * All six buffers must be distinct; dt > 0, nu >= 0, fx finite.  PP_FP64 and PP_FP32 plans
+ * (PP_FP32_REFINED: PS_EUNSUPPORTED). */
+poisson_status momentum_predictor(poisson_plan_t plan, void* u, void* v, void* w, void* ub, void* vb,
+                                  void* wb, double dt, double nu, double fx, void* stream);
+
+/* One full timestep of the fully explicit projection method (Sec. 2, Eqs. 3-7): the RK2
+ * predictor of momentum_predictor followed by projection_step (same dt) on u, v, w in place.
+ * p_out (may be NULL) receives the pressure.  Arguments as for the two calls. */
+poisson_status projection_timestep(poisson_plan_t plan, void* u, void* v, void* w, void* ub, void* vb,
+                                   void* wb, void* p_out, double dt, double nu, double fx, void* stream);
+
+/* End-to-end variant of projection_timestep on HOST buffers (as projection_step_host): copies
+ * u, v, w to the device buffers u_dev, v_dev, w_dev, runs projection_timestep with the device
+ * scratch ub, vb, wb, copies u, v, w (and p when p_host != NULL, through p_dev) back and
+ * synchronises `stream`. */
+poisson_status projection_timestep_host(poisson_plan_t plan, void* u_host, void* v_host, void* w_host,
+                                        void* p_host, void* u_dev, void* v_dev, void* w_dev, void* p_dev,
+                                        void* ub, void* vb, void* wb, double dt, double nu, double fx,
+                                        void* stream);
+
 /* Capacity of the library's built-in device workspace used by poisson_solve_static_ws. */
 #define POISSON_STATIC_WS_MAX_BYTES (8u * 1024u * 1024u)
 

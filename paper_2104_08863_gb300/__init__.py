@@ -96,6 +96,49 @@ class Plan:
               "projection_step")
         return p_out
 
+    def _stage_buffers(self, u, v, w, scratch):
+        self._check(u, self.cell_shape, "u")
+        self._check(v, self.v_shape, "v")
+        self._check(w, self.cell_shape, "w")
+        if scratch is None:
+            scratch = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        for t, shp, name in zip(scratch, (self.cell_shape, self.v_shape, self.cell_shape), ("ub", "vb", "wb")):
+            self._check(t, shp, name)
+        return scratch
+
+    def predict(self, u, v, w, dt: float, nu: float, fx: float, scratch=None, stream=None):
+        """In place: (u, v, w) <- the RK2 momentum predictor u_star (Eqs. 5-6).
+
+        scratch: optional (ub, vb, wb) device tensors of the field shapes for the first stage."""
+        ub, vb, wb = self._stage_buffers(u, v, w, scratch)
+        check(_native.lib().momentum_predictor(self._h, _ptr(u), _ptr(v), _ptr(w), _ptr(ub), _ptr(vb), _ptr(wb),
+                                               float(dt), float(nu), float(fx), _stream(stream)),
+              "momentum_predictor")
+
+    def timestep(self, u, v, w, dt: float, nu: float, fx: float, p_out=None, scratch=None, stream=None):
+        """In place: one full timestep (RK2 predictor, then the projection); returns p_out (or None)."""
+        ub, vb, wb = self._stage_buffers(u, v, w, scratch)
+        pp = 0
+        if p_out is not None:
+            self._check(p_out, self.cell_shape, "p_out")
+            pp = _ptr(p_out)
+        check(_native.lib().projection_timestep(self._h, _ptr(u), _ptr(v), _ptr(w), _ptr(ub), _ptr(vb), _ptr(wb), pp,
+                                                float(dt), float(nu), float(fx), _stream(stream)),
+              "projection_timestep")
+        return p_out
+
+    def timestep_host(self, u_h, v_h, w_h, dt: float, nu: float, fx: float, staging, scratch, p_h=None,
+                      stream=None):
+        """End-to-end timestep of HOST (pinned) tensors through the library's host entry point.
+
+        staging: (u_d, v_d, w_d, p_d) device tensors; scratch: (ub, vb, wb) device tensors."""
+        u_d, v_d, w_d, p_d = staging
+        ub, vb, wb = scratch
+        check(_native.lib().projection_timestep_host(
+            self._h, _ptr(u_h), _ptr(v_h), _ptr(w_h), _ptr(p_h) if p_h is not None else 0,
+            _ptr(u_d), _ptr(v_d), _ptr(w_d), _ptr(p_d) if p_d is not None else 0, _ptr(ub), _ptr(vb), _ptr(wb),
+            float(dt), float(nu), float(fx), _stream(stream)), "projection_timestep_host")
+
     def project_adjoint(self, gu, gv, gw, stream=None):
         """In place: g <- P^T g (the adjoint of the projection's velocity map)."""
         self._check(gu, self.cell_shape, "gu")

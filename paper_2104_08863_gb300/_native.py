@@ -24,8 +24,8 @@ POISSON_GENERIC_FFT = 0x4
 EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
     "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
-    "projection_step", "projection_step_adjoint", "projection_step_host", "poisson_device_status",
-    "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
+    "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
+    "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
 
@@ -70,6 +70,9 @@ def lib() -> ctypes.CDLL:
     L.projection_step.argtypes = [vp, vp, vp, vp, vp, d, vp]
     L.projection_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
     L.projection_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, vp]
+    L.momentum_predictor.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
+    L.projection_timestep.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
+    L.projection_timestep_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
     L.poisson_device_status.argtypes = [vp, vp]
     L.poisson_last_launch_count.argtypes = [vp]
     L.poisson_last_launch_count.restype = i
@@ -80,8 +83,8 @@ def lib() -> ctypes.CDLL:
     L.poisson_status_string.restype = ctypes.c_char_p
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
                  "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
-                 "projection_step", "projection_step_adjoint", "projection_step_host",
-                 "poisson_device_status", "poisson_plan_destroy"):
+                 "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
+                 "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_plan_destroy"):
         getattr(L, name).restype = i
     _LIB = L
     return L

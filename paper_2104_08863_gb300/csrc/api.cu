@@ -492,6 +492,74 @@ poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
   return PS_OK;
 }
 
+// Eqs. 4 and 7 on u, v, w in place (validated by the caller): divergence fused into the forward
+// x-transform, the solve, the gradient correction.
+poisson_status projection_impl(Exec& ex, void* u, void* v, void* w, void* p_out, double dt) {
+  const poisson_plan_s* pl = ex.pl;
+  cudaStream_t st = ex.st;
+  FwdArgs args = {};
+  args.u = u; args.v = v; args.w = w;
+  args.in_scale = 1.0 / dt;
+  if (pl->precision == PP_FP64) {
+    double* p = p_out ? (double*)p_out : (double*)(pl->ws + pl->off_pbuf);
+    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+    PP_RET((forward_and_core<double, double>(ex, FWD_DIV, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<double, double>(ex, INV_STORE, p, false)));
+    PP_TRY_N("gradient", launch_gradient<double>(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, st));
+  } else {
+    float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
+    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
+    PP_RET((forward_and_core<float, float>(ex, FWD_DIV, args, GAUGE_ZERO)));
+    PP_RET((inverse_x<float, float>(ex, INV_STORE, p, false)));
+    PP_TRY_N("gradient", launch_gradient<float>(pl->g, ex.dt, p, (float*)u, (float*)v, (float*)w, dt, st));
+  }
+  return PS_OK;
+}
+
+poisson_status check_timestep_args(const poisson_plan_s* pl, const void* u, const void* v, const void* w,
+                                   const void* ub, const void* vb, const void* wb, const void* p_out, double dt,
+                                   double nu, double fx) {
+  if (!pl || !u || !v || !w || !ub || !vb || !wb) return PS_EINVAL;
+  if (!pl->children.empty()) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!(dt > 0.0) || !isfinite(dt) || !(nu >= 0.0) || !isfinite(nu) || !isfinite(fx)) return PS_EINVAL;
+  const void* all[7] = {u, v, w, ub, vb, wb, p_out};
+  for (int a = 0; a < 7; ++a) {
+    if (all[a] && !aligned16(all[a])) return PS_EINVAL;
+    for (int b = 0; b < a; ++b)
+      if (all[a] && all[a] == all[b]) return PS_EINVAL;   // every buffer distinct
+  }
+  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  return PS_OK;
+}
+
+// Heun's RK2 (Eqs. 5-6) in two launches: (ub, vb, wb) = u + dt R(u), then in place
+// u = (u + ub + dt R(ub)) / 2.
+poisson_status predictor_impl(Exec& ex, void* u, void* v, void* w, void* ub, void* vb, void* wb, double dt,
+                              double nu, double fx) {
+  const poisson_plan_s* pl = ex.pl;
+  if (pl->precision == PP_FP64) {
+    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+    MomArgs<double> s1{(const double*)u, (const double*)v, (const double*)w, nullptr, nullptr, nullptr,
+                       (double*)ub, (double*)vb, (double*)wb, 0.0, 1.0, dt, nu, fx};
+    PP_TRY_N("momentum_1", launch_momentum<double>(pl->g, ex.dt, s1, ex.st));
+    MomArgs<double> s2{(const double*)ub, (const double*)vb, (const double*)wb, (const double*)u,
+                       (const double*)v, (const double*)w, (double*)u, (double*)v, (double*)w,
+                       0.5, 0.5, 0.5 * dt, nu, fx};
+    PP_TRY_N("momentum_2", launch_momentum<double>(pl->g, ex.dt, s2, ex.st));
+  } else {
+    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
+    MomArgs<float> s1{(const float*)u, (const float*)v, (const float*)w, nullptr, nullptr, nullptr,
+                      (float*)ub, (float*)vb, (float*)wb, 0.0, 1.0, dt, nu, fx};
+    PP_TRY_N("momentum_1", launch_momentum<float>(pl->g, ex.dt, s1, ex.st));
+    MomArgs<float> s2{(const float*)ub, (const float*)vb, (const float*)wb, (const float*)u,
+                      (const float*)v, (const float*)w, (float*)u, (float*)v, (float*)w,
+                      0.5, 0.5, 0.5 * dt, nu, fx};
+    PP_TRY_N("momentum_2", launch_momentum<float>(pl->g, ex.dt, s2, ex.st));
+  }
+  return PS_OK;
+}
+
 }  // namespace
 
 namespace pp {
@@ -528,24 +596,26 @@ poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, voi
   pl->launches = 0;
   pl->nev = 0;
   Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
-  cudaStream_t st = ex.st;
-  FwdArgs args = {};
-  args.u = u; args.v = v; args.w = w;
-  args.in_scale = 1.0 / dt;
-  if (pl->precision == PP_FP64) {
-    double* p = p_out ? (double*)p_out : (double*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
-    PP_RET((forward_and_core<double, double>(ex, FWD_DIV, args, GAUGE_ZERO)));
-    PP_RET((inverse_x<double, double>(ex, INV_STORE, p, false)));
-    PP_TRY_N("gradient", launch_gradient<double>(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, st));
-  } else {
-    float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
-    PP_RET((forward_and_core<float, float>(ex, FWD_DIV, args, GAUGE_ZERO)));
-    PP_RET((inverse_x<float, float>(ex, INV_STORE, p, false)));
-    PP_TRY_N("gradient", launch_gradient<float>(pl->g, ex.dt, p, (float*)u, (float*)v, (float*)w, dt, st));
-  }
-  return PS_OK;
+  return projection_impl(ex, u, v, w, p_out, dt);
+}
+
+poisson_status momentum_predictor(poisson_plan_t pl, void* u, void* v, void* w, void* ub, void* vb, void* wb,
+                                  double dt, double nu, double fx, void* stream) {
+  PP_RET(check_timestep_args(pl, u, v, w, ub, vb, wb, nullptr, dt, nu, fx));
+  pl->launches = 0;
+  pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  return predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx);
+}
+
+poisson_status projection_timestep(poisson_plan_t pl, void* u, void* v, void* w, void* ub, void* vb, void* wb,
+                                   void* p_out, double dt, double nu, double fx, void* stream) {
+  PP_RET(check_timestep_args(pl, u, v, w, ub, vb, wb, p_out, dt, nu, fx));
+  pl->launches = 0;
+  pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  PP_RET(predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx));
+  return projection_impl(ex, u, v, w, p_out, dt);
 }
 
 poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, void* gw, void* stream) {
@@ -588,6 +658,27 @@ poisson_status projection_step_host(poisson_plan_t pl, void* u_h, void* v_h, voi
   if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   PP_RET(projection_step(pl, u_d, v_d, w_d, p_h ? p_d : nullptr, dt, stream));
+  if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (p_h && cudaMemcpyAsync(p_h, p_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  return PS_OK;
+}
+
+poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h, void* w_h, void* p_h, void* u_d,
+                                        void* v_d, void* w_d, void* p_d, void* ub, void* vb, void* wb, double dt,
+                                        double nu, double fx, void* stream) {
+  if (!u_h || !v_h || !w_h) return PS_EINVAL;
+  if (p_h && !p_d) return PS_EINVAL;
+  PP_RET(check_timestep_args(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = pl->precision == PP_FP64 ? 8 : 4;
+  const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
+  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
   if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;

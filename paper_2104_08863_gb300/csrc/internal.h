@@ -161,6 +161,18 @@ cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, cons
 template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st);
 
+// One stage of Heun's RK2 momentum predictor (csrc/k_momentum.cu):
+//   out = alpha * base + beta * s + bdt * R(s),  R = -div(s s) + nu lap(s) + (fx, 0, 0).
+// base may be null (alpha = 0); out may alias base but not s.
+template <typename T> struct MomArgs {
+  const T *su, *sv, *sw;
+  const T *bu, *bv, *bw;
+  T *ou, *ov, *ow;
+  double alpha, beta, bdt, nu, fx;
+};
+template <typename T>
+cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st);
+
 }  // namespace pp
 
 // Host plan (opaque to callers of include/poisson.h).

@@ -1,0 +1,197 @@
+"""GPU parity of the RK2 momentum predictor and the full timestep (Sec. 2, Eqs. 3-7).
+
+Element by element against the oracle (``oracle.momentum``) on seeded inputs: grids whose x
+and z extents leave ragged CUDA tiles (32 x 8 columns) and whose wall-normal extent is split
+into several row chunks, plus the bench workload (512 x 384 x 512) checked on wall-normal slabs
+(the predictor is local: two stages reach two cells, so a slab with a two-row halo on each side
+is exact) and through properties of the projection that hold at any size.
+
+Tolerances, relative to the largest oracle magnitude: FP64 1e-12; FP32 2e-5 (each stage rounds
+O(10) FP32 terms of size <= max|u| and the projection's FP32 solve adds its 1e-6 level).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from oracle.momentum import rk2_predictor, timestep
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+NU = 1.0 / 550.0
+FX = 2.0 * NU
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_08863_gb300 import build as b
+    b.build()
+    import paper_2104_08863_gb300 as mod
+    return mod
+
+
+def relerr(got, want):
+    return float(np.max(np.abs(np.asarray(got) - want)) / np.max(np.abs(want)))
+
+
+def to_dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+SHAPES = [  # (nx, ny, nz, stretch): ragged x / z tiles, several row chunks, tiny ny
+    (32, 32, 32, 1.5),
+    (48, 20, 12, 2.0),
+    (96, 48, 24, 1.8),
+    (18, 64, 6, 2.2),
+    (64, 4, 16, 1.0),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_predictor_matches_oracle(P, shape, prec):
+    nx, ny, nz, s = shape
+    case = W.ChannelCase("t", nx, ny, nz, s)
+    faces = W.tanh_faces(ny, s)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.poiseuille_plus_noise(1, case)
+    dt = 2e-3
+    want = rk2_predictor(g, u, v, w, dt, NU, FX)
+    precision, dtype, tol = ((P.PP_FP64, torch.float64, 1e-12) if prec == "fp64"
+                             else (P.PP_FP32, torch.float32, 2e-5))
+    plan = P.Plan(nx, ny, nz, faces, precision=precision, device=DEV)
+    ut, vt, wt = to_dev(u, dtype), to_dev(v, dtype), to_dev(w, dtype)
+    plan.predict(ut, vt, wt, dt, NU, FX)
+    torch.cuda.synchronize()
+    scale = max(np.max(np.abs(a)) for a in want)
+    for got, ref in zip((ut, vt, wt), want):
+        err = float(np.max(np.abs(got.double().cpu().numpy() - ref))) / scale
+        assert err <= tol, err
+    assert plan.last_launch_count == 2
+    # v's walls are boundary values
+    assert torch.equal(vt[0], to_dev(v[0], dtype)) and torch.equal(vt[-1], to_dev(v[-1], dtype))
+
+
+@pytest.mark.parametrize("shape", SHAPES[:4])
+def test_fp64_timestep_matches_oracle_over_three_steps(P, shape):
+    nx, ny, nz, s = shape
+    case = W.ChannelCase("t", nx, ny, nz, s)
+    faces = W.tanh_faces(ny, s)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.poiseuille_plus_noise(1, case)
+    dt = 1e-3
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, tridiag=P.PT_PDD_EXACT,
+                  pdd_parts=4 if ny % 4 == 0 and ny >= 8 else 1, device=DEV)
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    pt = torch.empty(ny, nz, nx, dtype=torch.float64, device=DEV)
+    scratch = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    for _ in range(3):
+        u, v, w, p = timestep(g, u, v, w, dt, NU, FX)
+        plan.timestep(ut, vt, wt, dt, NU, FX, p_out=pt, scratch=scratch)
+    torch.cuda.synchronize()
+    scale = max(np.max(np.abs(a)) for a in (u, v, w))
+    for got, ref in zip((ut, vt, wt), (u, v, w)):
+        assert float(np.max(np.abs(got.cpu().numpy() - ref))) / scale <= 1e-12
+    assert relerr(pt.cpu().numpy(), p) <= 1e-12
+    d = oracle.divergence(g, ut.cpu().numpy(), vt.cpu().numpy(), wt.cpu().numpy())
+    assert np.max(np.abs(d)) <= 1e-11 * scale / min(g.dx, g.dz, g.dy.min())
+
+
+def test_fp32_timestep_matches_oracle(P):
+    nx, ny, nz, s = 64, 32, 32, 1.8
+    case = W.ChannelCase("t", nx, ny, nz, s)
+    faces = W.tanh_faces(ny, s)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.poiseuille_plus_noise(1, case)
+    dt = 1e-3
+    u1, v1, w1, p1 = timestep(g, u, v, w, dt, NU, FX)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32, device=DEV)
+    ut, vt, wt = (to_dev(a, torch.float32) for a in (u, v, w))
+    pt = torch.empty(ny, nz, nx, dtype=torch.float32, device=DEV)
+    plan.timestep(ut, vt, wt, dt, NU, FX, p_out=pt)
+    torch.cuda.synchronize()
+    scale = max(np.max(np.abs(a)) for a in (u1, v1, w1))
+    for got, ref in zip((ut, vt, wt), (u1, v1, w1)):
+        assert float(np.max(np.abs(got.double().cpu().numpy() - ref))) / scale <= 2e-5
+    assert relerr(pt.double().cpu().numpy(), p1) <= 2e-5
+
+
+def test_timestep_argument_checks(P):
+    nx, ny, nz = 32, 16, 16
+    faces = W.tanh_faces(ny, 1.5)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, device=DEV)
+    u = torch.zeros(ny, nz, nx, dtype=torch.float64, device=DEV)
+    v = torch.zeros(ny + 1, nz, nx, dtype=torch.float64, device=DEV)
+    w = torch.zeros_like(u)
+    ub, vb, wb = torch.zeros_like(u), torch.zeros_like(v), torch.zeros_like(w)
+    with pytest.raises(P.PoissonError) as e:
+        plan.timestep(u, v, w, 1e-3, NU, FX, scratch=(u, vb, wb))    # aliasing scratch
+    assert e.value.code == P._native.PS_EINVAL
+    for dt, nu, fx in [(0.0, NU, FX), (1e-3, -1.0, FX), (1e-3, NU, float("nan"))]:
+        with pytest.raises(P.PoissonError) as e:
+            plan.timestep(u, v, w, dt, nu, fx, scratch=(ub, vb, wb))
+        assert e.value.code == P._native.PS_EINVAL
+    ref = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, device=DEV)
+    with pytest.raises(P.PoissonError) as e:
+        ref.timestep(u, v, w, 1e-3, NU, FX, scratch=(ub, vb, wb))
+    assert e.value.code == P._native.PS_EUNSUPPORTED
+    # a zero state with no forcing stays zero
+    plan.timestep(u, v, w, 1e-3, NU, 0.0, scratch=(ub, vb, wb))
+    torch.cuda.synchronize()
+    assert float(u.abs().max()) == 0.0 and float(v.abs().max()) == 0.0 and float(w.abs().max()) == 0.0
+
+
+def _slab_predictor(g_full, faces, u, v, w, j0, j1, dt):
+    """Oracle predictor on rows j0..j1-1 from a slab with a two-row halo (exact: radius 2)."""
+    ny = g_full.ny
+    lo, hi = max(0, j0 - 2), min(ny, j1 + 2)
+    gs = oracle.Grid(g_full.nx, g_full.nz, faces[lo:hi + 1])
+    us, vs, ws = rk2_predictor(gs, u[lo:hi], v[lo:hi + 1], w[lo:hi], dt, NU, FX)
+    return us[j0 - lo:j1 - lo], vs[j0 - lo:j1 - lo], ws[j0 - lo:j1 - lo]
+
+
+def test_fp64_timestep_512x384x512_slabs_and_invariants(P):
+    """The bench workload, in its launch configuration: predictor on wall and interior slabs,
+    then the projection (zero divergence, u = u* - dt G p, sampled pressure modes)."""
+    from test_gpu_fullsize import mode_coeffs, oracle_mode_solve
+    case = W.CHANNEL_512
+    faces = W.tanh_faces(case.ny, case.stretch)
+    g = oracle.Grid(case.nx, case.nz, faces)
+    dt = 1e-4
+    u, v, w = W.poiseuille_plus_noise(1, case)
+    plan = P.Plan(case.nx, case.ny, case.nz, faces, precision=P.PP_FP64, tridiag=P.PT_PDD_EXACT, pdd_parts=8,
+                  device=DEV)
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    scratch = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    plan.predict(ut, vt, wt, dt, NU, FX, scratch=scratch)
+    torch.cuda.synchronize()
+    us_g, vs_g, ws_g = (t.cpu().numpy() for t in (ut, vt, wt))
+    scale = np.max(np.abs(u))
+    for j0, j1 in [(0, 6), (190, 196), (378, 384)]:
+        want = _slab_predictor(g, faces, u, v, w, j0, j1, dt)
+        got = (us_g[j0:j1], vs_g[j0:j1], ws_g[j0:j1])
+        for a, b in zip(got, want):
+            assert float(np.max(np.abs(a - b))) <= 1e-12 * scale
+    # the full timestep from the same initial state
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    pt = torch.empty(case.ny, case.nz, case.nx, dtype=torch.float64, device=DEV)
+    plan.timestep(ut, vt, wt, dt, NU, FX, p_out=pt, scratch=scratch)
+    torch.cuda.synchronize()
+    p = pt.cpu().numpy()
+    u1, v1, w1 = (t.cpu().numpy() for t in (ut, vt, wt))
+    del ut, vt, wt, pt, scratch
+    f = oracle.divergence(g, us_g, vs_g, ws_g) / dt
+    d1 = oracle.divergence(g, u1, v1, w1)
+    assert np.max(np.abs(d1)) <= 1e-12 * np.max(np.abs(f)) * dt
+    gx, gy, gz = oracle.gradient(g, p)
+    assert np.max(np.abs(u1 - (us_g - dt * gx))) <= 1e-13 * scale
+    assert np.max(np.abs(v1 - (vs_g - dt * gy))) <= 1e-13 * scale
+    assert np.max(np.abs(w1 - (ws_g - dt * gz))) <= 1e-13 * scale
+    pmax = np.max(np.abs(p))
+    worst = 0.0
+    for kx, kz in [(1, 0), (0, 1), (3, 5), (255, 511)]:
+        want = oracle_mode_solve(g, mode_coeffs(f, kx, kz), kx, kz)
+        worst = max(worst, np.max(np.abs(mode_coeffs(p, kx, kz) - want)) / (pmax * case.nx * case.nz))
+    assert worst <= 1e-12, worst
