@@ -71,7 +71,9 @@ typedef struct {
   const double* y_faces;    /* host pointer, ny+1 values; copied during poisson_plan_create */
   int precision;            /* poisson_precision                                         */
   int tridiag;              /* poisson_tridiag                                           */
-  int pdd_parts;            /* PDD sub-blocks per system (divides ny); 0 = automatic     */
+  int pdd_parts;            /* PDD sub-blocks per system (divides ny; <= 32, or <= 256   */
+                            /* for FP32 plans with ny/P in {1,2,3,4,6,8,12,16,24});      */
+                            /* 0 = automatic                                             */
   int fp64_low_modes;       /* PP_FP32*: systems with kx <= L and |kz| <= L run in FP64  */
   int refine_steps;         /* PP_FP32_REFINED: number of residual corrections (>= 1)    */
   unsigned flags;           /* POISSON_CHECK_FINITE                                      */
@@ -181,7 +183,8 @@ poisson_status poisson_plan_batched(const poisson_desc* descs, int count, poisso
 poisson_status poisson_solve_batched(poisson_plan_t plan, const void* const* rhs, void* const* p, void* stream);
 
 /* Autotuner: for the grid of `desc`, time poisson_solve with every candidate PDD partition
- * count (1 and the divisors P of ny with 2 <= P <= 32 and ny/P >= 4) and both FFT tilings
+ * count (1, the divisors P of ny with 2 <= P <= 32 and ny/P >= 4 and, for FP32 plans, the
+ * divisors whose block height ny/P is one of 1, 2, 3, 4, 6, 8, 12, 16, 24) and both FFT tilings
  * (specialised, generic) on `stream`, and return the fastest in *pdd_parts and *flags (the
  * POISSON_GENERIC_FFT bit) with its time in *ms.  It allocates and frees its own device buffers
  * (set-up time, not the solve path) and synchronises `stream`. */

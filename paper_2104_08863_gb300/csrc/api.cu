@@ -41,7 +41,13 @@ bool factor(int L, FftFactors& f) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int auto_parts(int ny) {
+// Automatic PDD partition.  FP64 (factored kernel, FP64-issue bound): the most blocks with at
+// least 48 rows each.  FP32 (register kernel): blocks of the largest supported height <= 24.
+int auto_parts(int ny, int precision) {
+  if (precision != PP_FP64) {
+    for (int P = 1; P <= 256; ++P)
+      if (ny % P == 0 && ny / P <= 24 && pp::reg_tridiag_ok(ny, P)) return P;
+  }
   int best = 1;
   for (int P = 2; P <= 32; ++P)
     if (ny % P == 0 && ny / P >= 48) best = P;
@@ -103,6 +109,7 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
   dt.f.c_lo = (const float*)(tb + to[19]);
   dt.d.a_lo = nullptr;
   dt.d.c_lo = nullptr;
+  dt.red_f = pl->has_tri ? nullptr : (const float*)(base + pl->off_red);
   dt.status = (int*)(base + pl->off_status);
   dt.acc = (double*)(base + pl->off_acc);
   dt.tri_d = TriFactors<double>{};
@@ -116,7 +123,7 @@ DevTables bind_tables(const poisson_plan_s* pl, unsigned char* base) {
       f.mult = t; f.kappa = t + rows; f.rb = t + 2 * rows; f.gv = t + 3 * rows;
       f.vF = t + 4 * rows; f.vL = f.vF + blks; f.wF = f.vL + blks; f.wL = f.wF + blks;
       f.nsys = (int)nsys;
-    } else {
+    } else if (pl->has_tri) {
       float* t = (float*)(base + pl->off_tri);
       TriFactors<float>& f = dt.tri_f;
       f.mult = nullptr; f.kappa = nullptr; f.rb = t; f.gv = t + rows;
@@ -174,8 +181,11 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   int P = 1;
   if (d->tridiag == PT_THOMAS) P = 1;
   else if (d->pdd_parts > 0) P = d->pdd_parts;
-  else P = auto_parts(g.ny);
-  if (P > 32 || g.ny % P != 0) { delete pl; return PS_EUNSUPPORTED; }
+  else P = auto_parts(g.ny, d->precision);
+  if (g.ny % P != 0 || (P > 32 && !(d->precision != PP_FP64 && pp::reg_tridiag_ok(g.ny, P)))) {
+    delete pl;
+    return PS_EUNSUPPORTED;
+  }
   pl->parts = P;
   int L = -1;
   if (d->precision != PP_FP64) {
@@ -287,8 +297,12 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   {   // per-mode PDD factors: FP64 plans 4 per row + 4 per block; FP32 plans 2 per row + 4 per block
     const size_t nsys = (size_t)g.nz * g.ncols;
     pl->off_tri = off;
+    // FP32 plans whose blocks fit in registers build their factors on the fly (no tables)
+    pl->has_tri = d->precision == PP_FP64 || !pp::reg_tridiag_ok(ny, P);
     if (d->precision == PP_FP64) off = align_up(off + 8 * nsys * (4 * (size_t)ny + 4 * (size_t)P), 256);
-    else off = align_up(off + 4 * nsys * (2 * (size_t)ny + 4 * (size_t)P), 256);
+    else if (pl->has_tri) off = align_up(off + 4 * nsys * (2 * (size_t)ny + 4 * (size_t)P), 256);
+    pl->off_red = off;
+    if (!pl->has_tri) off = align_up(off + pp::reduced_table_bytes(g, P), 256);
   }
   pl->ws_bytes = off;
   pl->ws = nullptr;
@@ -320,7 +334,12 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return PS_ECUDA;
   pl->ws = base;
   pl->dt = pp::bind_tables(pl, base);
-  if (pl->off_tri) {
+  if (!pl->has_tri && pl->parts > 1) {
+    if (launch_reduced_setup(pl->g, pl->dt, pl->parts, (float*)(base + pl->off_red), st) != cudaSuccess)
+      return PS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  }
+  if (pl->has_tri) {
     if (launch_tridiag_setup(pl->g, pl->dt, pl->parts, st) != cudaSuccess) return PS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
   }
@@ -397,7 +416,8 @@ poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
   PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, spec, st));
+  if (pl->has_tri) PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, spec, st));
+  else PP_TRY_N("tridiag_pdd", launch_tridiag_reg_f32(g, ex.dt, pl->parts, pl->low, spec, st));
   if (pl->low >= 0) {
     cplx<double>* scr = (cplx<double>*)(ex.ws + pl->off_scratch);
     PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, st));

@@ -158,8 +158,12 @@ poisson_status poisson_autotune(const poisson_desc* desc, void* stream, int* pdd
   if (!desc || !pdd_parts || !flags) return PS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int> cands{1};
-  for (int P = 2; P <= 32; ++P)
-    if (desc->ny % P == 0 && desc->ny / P >= 4) cands.push_back(P);
+  for (int P = 2; P <= 256; ++P) {
+    if (desc->ny % P) continue;
+    const bool factored = P <= 32 && desc->ny / P >= 4;
+    const bool reg = desc->precision != PP_FP64 && pp::reg_tridiag_ok(desc->ny, P);
+    if (factored || reg) cands.push_back(P);
+  }
   const size_t cells = (size_t)desc->nx * desc->ny * desc->nz;
   const size_t es = desc->precision == PP_FP32 ? 4 : 8;
   unsigned char* io = nullptr;

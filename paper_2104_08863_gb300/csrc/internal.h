@@ -46,6 +46,7 @@ struct DevTables {
   double* acc;             // accumulators of the refined solve: [0] <f>, [1] sum_jki dy_j p_jki
   TriFactors<double> tri_d;  // FP64 plans
   TriFactors<float> tri_f;   // FP32 and FP32-refined plans
+  const float* red_f;        // FP32 register-kernel plans: per-mode LU of the reduced interface system
 };
 
 struct Geometry {
@@ -138,6 +139,21 @@ cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int 
 cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                         cplx<float>* spec, cudaStream_t st);
 
+// FP32 PDD with each block of m = ny/P rows held in one thread's registers and its factors
+// computed on the fly (no factor tables): m in {1, 2, 3, 4, 6, 8, 12, 16, 24}, P <= 256, S = 256/P
+// systems per CTA (at least 1).  Other (ny, P) use the factored kernel with tables.
+inline bool reg_tridiag_ok(int ny, int P) {
+  if (P < 1 || P > 256 || ny % P) return false;
+  const int m = ny / P;
+  return m == 1 || m == 2 || m == 3 || m == 4 || m == 6 || m == 8 || m == 12 || m == 16 || m == 24;
+}
+inline int reg_systems_per_cta(int P) { return P >= 256 ? 1 : 256 / P; }
+cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                   cplx<float>* spec, cudaStream_t st);
+// Bytes of the reduced-system table of the register kernel, and its FP64 set-up (once per plan).
+size_t reduced_table_bytes(const Geometry& g, int parts);
+cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, float* tab, cudaStream_t st);
+
 // FP64 re-solve of the low-mode list on FP32 spectral data (intermediates in FP64 scratch).
 cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                  cplx<float>* spec, cplx<double>* scratch, cudaStream_t st);
@@ -185,7 +201,8 @@ struct poisson_plan_s {
   std::vector<double> faces, dy, h, a, c, lamx, lamz;
   std::vector<unsigned char> host_tables;   // staging image of the device tables
   // workspace layout (byte offsets)
-  size_t off_spec, off_pbuf, off_pbuf2, off_scratch, off_tables, off_status, off_acc, off_tri, ws_bytes;
+  size_t off_spec, off_pbuf, off_pbuf2, off_scratch, off_tables, off_status, off_acc, off_tri, off_red, ws_bytes;
+  bool has_tri;   // per-mode PDD factor tables in the workspace (FP64 plans; FP32 plans with m = ny/P outside the register kernel's set)
   size_t tab_offsets[32];
   unsigned char* ws;
   pp::DevTables dt;

@@ -406,6 +406,217 @@ __global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int
   }
 }
 
+// ---- FP32 PDD with thread-private blocks (the FP32 production path) -------------------------
+// One thread owns one block of M rows of one system.  It copies its M rows into a private slice
+// of shared memory with 8-byte cp.async (all M copies in flight, no register staging; layout
+// [row][thread], so every shared access of a warp is conflict-free), eliminates forward while
+// building the block's pivots and spike on the fly in FP32 (margin recurrence, reciprocal by
+// MUFU plus one Newton step) and keeping them in registers, exchanges the block-end values
+// through shared memory for the exact reduced interface system, and sweeps back, storing each
+// result straight to global memory.  The spectrum crosses HBM once in each direction and no
+// factor table is read.  Threads are numbered block-major (tid = b * S + s), so a warp's row
+// accesses are S-system contiguous segments.
+
+__device__ __forceinline__ float rcp_nr(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  const float e = fmaf(-x, r, 1.f);
+  return fmaf(r, e, r);
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Per-mode LU of the reduced interface system, built once per plan in FP64 (RHS-independent).
+// For interface i (between blocks i and i+1) of system sys, entry k of table[(i*5 + k)*nsys + sys]:
+//   0: vL_i      the spike v of block i at its last row
+//   1: inv_i     1 / (1 - d01 d10),  d01 = -wL_i - vL_i wF_i X01_{i-1},  d10 = -vF_{i+1}
+//   2: X01_i     -d01 inv_i
+//   3: X10_i     -d10 inv_i
+//   4: wF_{i+1}  the spike w of block i+1 at its first row (0 for the last interface)
+// One thread per system walks the blocks in order, keeping two blocks' spike values.
+__device__ void block_spikes64(const double* a, const double* c, double sigma, int r0, int m, double& vF,
+                               double& vL, double& wF, double& wL) {
+  double e = a[r0] + sigma, gvv = a[r0], rbp = 0.0, run = 1.0, kap = 0.0;
+  vF = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const int j = r0 + i;
+    if (i > 0) {
+      const double mult = a[j] * rbp;
+      e = sigma + mult * e;
+      gvv = mult * gvv;
+    }
+    const double rb = 1.0 / (c[j] + e);
+    kap = run * rb;
+    vF += kap * gvv;
+    run *= c[j] * rb;
+    rbp = rb;
+  }
+  vL = gvv * rbp;
+  wF = kap * c[r0 + m - 1];
+  wL = c[r0 + m - 1] * rbp;
+}
+
+__global__ void __launch_bounds__(128) k_reduced_setup(Geometry g, int P, int m, const double* __restrict__ a,
+                                                      const double* __restrict__ c, const double* __restrict__ lamx,
+                                                      const double* __restrict__ lamz, float* __restrict__ tab) {
+  const int nsys = g.nz * g.ncols;
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  int kx, kz;
+  sys_to_mode(sys, g.ncols, kx, kz);
+  const double sigma = (kx == 0 && kz == 0) ? 1.0 : -(lamx[kx] + lamz[kz]);
+  double vF0, vL0, wF0, wL0;
+  block_spikes64(a, c, sigma, 0, m, vF0, vL0, wF0, wL0);
+  double pX01 = 0.0;
+  for (int i = 0; i < P - 1; ++i) {
+    double vF1, vL1, wF1, wL1;
+    block_spikes64(a, c, sigma, (i + 1) * m, m, vF1, vL1, wF1, wL1);
+    const double d01 = -wL0 - vL0 * wF0 * pX01, d10 = -vF1;
+    const double inv = 1.0 / (1.0 - d01 * d10);
+    const double X01 = -d01 * inv, X10 = -d10 * inv;
+    float* t = tab + (size_t)(i * 5) * nsys + sys;
+    t[0] = float(vL0);
+    t[(size_t)nsys] = float(inv);
+    t[(size_t)2 * nsys] = float(X01);
+    t[(size_t)3 * nsys] = float(X10);
+    t[(size_t)4 * nsys] = i + 1 < P - 1 ? float(wF1) : 0.f;
+    pX01 = X01;
+    vF0 = vF1; vL0 = vL1; wF0 = wF1; wL0 = wL1;
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) k_tridiag_reg(Geometry g, int P, int S, int low, const float* __restrict__ a,
+                                                        const float* __restrict__ c, const double* __restrict__ lamx,
+                                                        const double* __restrict__ lamz, const float* __restrict__ rtab,
+                                                        cplx<float>* __restrict__ spec) {
+  // shared: the interface arrays (6 x NT floats), the CTA's slice of the reduced-system table
+  // (5 (P-1) S floats, [i][k][s]), then the blocks' rows [row][thread]
+  extern __shared__ __align__(16) float red_s[];
+  enum { R_XFR, R_XFI, R_XLR, R_XLI, R_ZR, R_ZI };
+  const int NT = P * S;
+#define RED(k, idx) red_s[(k) * NT + (idx)]
+  float* tsh = red_s + 6 * NT;
+  float2* Xs = reinterpret_cast<float2*>(tsh + ((5 * (P - 1) * S + 1) & ~1));
+  const int nsys = g.nz * g.ncols;
+  const int tid = threadIdx.x;
+  const int b = tid / S, s = tid - b * S;
+  const int sys0 = blockIdx.x * S;
+  const int sys = sys0 + s;
+  int kx = 0, kz = 0;
+  bool active = sys < nsys;
+  if (active) {
+    sys_to_mode(sys, g.ncols, kx, kz);
+    if ((kx == 0 && kz == 0) || is_low(kx, kz, g.nz, low)) active = false;
+  }
+  const size_t rstride = (size_t)g.nz * g.pitch;
+  float2* col = reinterpret_cast<float2*>(spec + (size_t)kz * g.pitch + kx);
+  const int r0 = b * M;
+  if (active) {
+    const float2* src = col + (size_t)r0 * rstride;
+#pragma unroll 1
+    for (int i = 0; i < M; ++i, src += rstride) cp_async8(&Xs[i * NT + tid], src);
+  }
+  for (int q = tid; q < 5 * (P - 1) * S; q += NT) {   // the reduced-system table slice
+    const int ik = q / S, qs = q - ik * S;
+    if (sys0 + qs < nsys) cp_async4(&tsh[q], &rtab[(size_t)ik * nsys + sys0 + qs]);
+  }
+  float rbv[M], gvv[M];
+  if (active) {
+    const float sigma = float(-(lamx[kx] + lamz[kz]));
+    cp_async_wait_all();
+    float e = a[r0] + sigma, gv = a[r0], rb = rcp_nr(c[r0] + e);
+    float run = 1.f;
+    float2 gg = make_float2(0.f, 0.f);
+    float2 xF = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int j = r0 + i;
+      const float cj = c[j];
+      const float2 F = Xs[i * NT + tid];
+      float mult = 0.f;
+      if (i > 0) {
+        mult = a[j] * rb;
+        e = fmaf(mult, e, sigma);
+        gv = mult * gv;
+        rb = rcp_nr(cj + e);
+      }
+      gg = make_float2(fmaf(mult, gg.x, -F.x), fmaf(mult, gg.y, -F.y));
+      Xs[i * NT + tid] = gg;
+      rbv[i] = rb;
+      gvv[i] = gv;
+      const float kap = run * rb;
+      xF.x = fmaf(kap, gg.x, xF.x);
+      xF.y = fmaf(kap, gg.y, xF.y);
+      run *= cj * rb;
+    }
+    RED(R_XFR, tid) = xF.x; RED(R_XFI, tid) = xF.y;
+    RED(R_XLR, tid) = gg.x * rb; RED(R_XLI, tid) = gg.y * rb;
+  } else {
+    cp_async_wait_all();
+  }
+  float2 alpha = make_float2(0.f, 0.f), beta = make_float2(0.f, 0.f);
+  if (P > 1) {
+    __syncthreads();
+    if (b == 0 && active) {
+      // forward: y_i = [inv X01; X10 inv] (xL_i + vL_i y0_{i-1}, xF_{i+1}); y0 kept in R_Z, y1 in
+      // the block's xF slot (no longer needed)
+      float2 py0 = make_float2(0.f, 0.f);
+      for (int i = 0; i < P - 1; ++i) {
+        const int ii = i * S + s, in = ii + S;
+        const float* t = tsh + i * 5 * S + s;
+        const float vL = t[0], inv = t[S], X01 = t[2 * S], X10 = t[3 * S];
+        const float q0x = fmaf(vL, py0.x, RED(R_XLR, ii)), q0y = fmaf(vL, py0.y, RED(R_XLI, ii));
+        const float q1x = RED(R_XFR, in), q1y = RED(R_XFI, in);
+        py0 = make_float2(fmaf(inv, q0x, X01 * q1x), fmaf(inv, q0y, X01 * q1y));
+        RED(R_ZR, ii) = py0.x; RED(R_ZI, ii) = py0.y;
+        RED(R_XFR, in) = fmaf(X10, q0x, inv * q1x); RED(R_XFI, in) = fmaf(X10, q0y, inv * q1y);
+      }
+      // backward: z1_i = y1_i + wF_{i+1} inv_i z1_{i+1}, z0_i = y0_i + wF_{i+1} X01_i z1_{i+1};
+      // alpha of block i+1 = z0_i (stored in its R_XL slot), beta of block i = z1_i (R_Z slot)
+      float2 z1n = make_float2(0.f, 0.f);
+      for (int i = P - 2; i >= 0; --i) {
+        const int ii = i * S + s, in = ii + S;
+        const float* t = tsh + i * 5 * S + s;
+        const float inv = t[S], X01 = t[2 * S], tw = t[4 * S];
+        const float a0 = tw * X01, a1 = tw * inv;
+        const float z0x = fmaf(a0, z1n.x, RED(R_ZR, ii)), z0y = fmaf(a0, z1n.y, RED(R_ZI, ii));
+        z1n = make_float2(fmaf(a1, z1n.x, RED(R_XFR, in)), fmaf(a1, z1n.y, RED(R_XFI, in)));
+        RED(R_XLR, in) = z0x; RED(R_XLI, in) = z0y;
+        RED(R_ZR, ii) = z1n.x; RED(R_ZI, ii) = z1n.y;
+      }
+    }
+    __syncthreads();
+    if (b > 0) alpha = make_float2(RED(R_XLR, tid), RED(R_XLI, tid));
+    if (b < P - 1) beta = make_float2(RED(R_ZR, tid), RED(R_ZI, tid));
+  }
+#undef RED
+  if (active) {
+    float2 xn = beta;
+    float2* dst = col + (size_t)(r0 + M - 1) * rstride;
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+      const float cj = c[r0 + i];
+      const float2 G = Xs[i * NT + tid];
+      const float tx = fmaf(cj, xn.x, fmaf(alpha.x, gvv[i], G.x));
+      const float ty = fmaf(cj, xn.y, fmaf(alpha.y, gvv[i], G.y));
+      xn = make_float2(tx * rbv[i], ty * rbv[i]);
+      *dst = xn;
+      dst -= rstride;
+    }
+  }
+}
+
 // The (0, 0) mode: T p = F - mean with sum_j dy_j p_j = 0 (compatibility and gauge), by the
 // exact flux prefix sums  q_j = sum_{l<=j} dy_l F^c_l,  p_0 = 0,  p_{j+1} = p_j + h_{j+1} q_j,
 // followed by removal of the dy-weighted mean.  One warp, FP64, chunked warp scans.
@@ -578,6 +789,44 @@ static cudaError_t launch_factored(const Geometry& g, const T* a, const T* c, co
   cudaError_t e;
   if ((e = prep(kern, smem)) != cudaSuccess) return e;
   kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, low, a, c, tf, spec);
+  return cudaGetLastError();
+}
+
+size_t reduced_table_bytes(const Geometry& g, int parts) {
+  return parts > 1 ? (size_t)5 * (parts - 1) * g.nz * g.ncols * sizeof(float) : 0;
+}
+
+cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, float* tab, cudaStream_t st) {
+  if (parts <= 1) return cudaSuccess;
+  const int nsys = g.nz * g.ncols;
+  k_reduced_setup<<<(nsys + 127) / 128, 128, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c, tb.lamx, tb.lamz, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+                                   cplx<float>* spec, cudaStream_t st) {
+  if (!reg_tridiag_ok(g.ny, parts)) return cudaErrorNotSupported;
+  const int m = g.ny / parts;
+  const int S = reg_systems_per_cta(parts);
+  const int nt = parts * S;
+  const size_t tabf = ((size_t)5 * (parts - 1) * S + 1) & ~(size_t)1;
+  const size_t smem = (size_t)6 * nt * sizeof(float) + tabf * sizeof(float) + (size_t)m * 8 * nt;
+  const int nsys = g.nz * g.ncols;
+  const int blocks = (nsys + S - 1) / S;
+#define PP_REG_CASE(MM)                                                                                         \
+  case MM: {                                                                                                    \
+    cudaError_t e = prep(k_tridiag_reg<MM>, smem);                                                              \
+    if (e != cudaSuccess) return e;                                                                             \
+    k_tridiag_reg<MM><<<blocks, nt, smem, st>>>(g, parts, S, low_modes, tb.f.a, tb.f.c, tb.lamx, tb.lamz,       \
+                                                tb.red_f, spec);                                                \
+    break;                                                                                                      \
+  }
+  switch (m) {
+    PP_REG_CASE(1) PP_REG_CASE(2) PP_REG_CASE(3) PP_REG_CASE(4) PP_REG_CASE(6) PP_REG_CASE(8)
+    PP_REG_CASE(12) PP_REG_CASE(16) PP_REG_CASE(24)
+    default: return cudaErrorNotSupported;
+  }
+#undef PP_REG_CASE
   return cudaGetLastError();
 }
 
