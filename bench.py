@@ -133,7 +133,7 @@ def kernel_model(name: str, nx: int, ny: int, nz: int):
     N = nx * ny * nz
     Ns = (nx // 2 + 1) * ny * nz
     plane = nx * nz
-    if name == "fwd_x":        # read u, v (ny+1 planes), w; write the half spectrum
+    if name == "fwd_x_div":    # read u, v (ny+1 planes), w; write the half spectrum
         return 8 * (3 * N + plane) + 16 * Ns, 2.5 * N * math.log2(nx)
     if name in ("fft_z_fwd", "fft_z_inv"):
         return 32 * Ns, 5.0 * Ns * math.log2(nz)
@@ -308,7 +308,7 @@ def run_gpu(args):
     t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
     if t_alu > t_hbm:
         achieved = flops / (avg_ms * 1e-3) / 1e12
-        tr = FWD_X_FP64_TRAFFIC if dom == "fwd_x" else KERNEL_TRAFFIC.get(dom)
+        tr = FWD_X_FP64_TRAFFIC if dom == "fwd_x_div" else KERNEL_TRAFFIC.get(dom)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": tr["bytes"] if tr else None,
                 "traffic_source": tr["source"] if tr else None,
@@ -472,6 +472,9 @@ PROFILE_CASES = {
     "fp64_projection_512": (W.CHANNEL_512, 0, 0, "projection"),
     "fp32_solve_512": (W.CHANNEL_512, 1, 0, "solve"),
     "fp32_refined_solve_512": (W.CHANNEL_512, 2, 1, "solve"),
+    # the 768-row wall-normal grid of the 1536x768x1024 precision form on a 256x256 plane
+    "fp32_refined_solve_256x768x256": (W.ChannelCase("channel_256x768x256_tanh2.2", 256, 768, 256, 2.2), 2, 1,
+                                       "solve"),
 }
 
 
@@ -484,8 +487,9 @@ def profile_case(name: str, repeats: int = 2):
     case, prec, steps, kind = PROFILE_CASES[name]
     dev = torch.device("cuda", 0)
     faces = W.tanh_faces(case.ny, case.stretch)
-    plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=PDD_PARTS
-                  if case.ny % PDD_PARTS == 0 else 0, refine_steps=max(steps, 1), device=dev)
+    parts = PDD_PARTS if (prec == P.PP_FP64 and case.ny % PDD_PARTS == 0) else 0
+    plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=parts,
+                  refine_steps=max(steps, 1), device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     dtype = torch.float32 if prec == P.PP_FP32 else torch.float64

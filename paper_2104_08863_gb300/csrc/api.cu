@@ -431,7 +431,8 @@ template <typename T, typename TI>
 poisson_status forward_and_core(Exec& ex, FwdMode mode, const FwdArgs& args, GaugeMode gauge) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   cudaStream_t st = ex.st;
-  PP_TRY_N("fwd_x", (launch_fwd_x<T, TI>(ex.pl->g, ex.dt, ex.pl->fm, mode, args, spec, st)));
+  static const char* const fwd_names[] = {"fwd_x", "fwd_x_div", "fwd_x_resid", "fwd_x_gradt"};
+  PP_TRY_N(fwd_names[mode], (launch_fwd_x<T, TI>(ex.pl->g, ex.dt, ex.pl->fm, mode, args, spec, st)));
   return spectral_core<T>(ex, spec, gauge);
 }
 
@@ -440,7 +441,9 @@ poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate, PairA
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   const double scale = 1.0 / ((double)ex.pl->g.nx * (double)ex.pl->g.nz);
   cudaStream_t st = ex.st;
-  PP_TRY_N("inv_x", (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st, pair)));
+  static const char* const inv_names[] = {"inv_x", "inv_x_accum", "inv_x_final"};
+  PP_TRY_N(inv_names[mode], (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st,
+                                                 pair)));
   return PS_OK;
 }
 
@@ -504,8 +507,8 @@ poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
       if (r < pl->refine) {
         PP_RET((inverse_x<float, float>(ex, r == 1 ? INV_STORE : INV_ACCUM, lo, true)));
       } else {
-        PairArgs pair{hi, r >= 2 ? lo : nullptr};
-        PP_RET((inverse_x<float, double>(ex, INV_FINAL, (double*)p, true, pair)));
+        PairArgs pair{hi, r >= 2 ? lo : nullptr};   // the last pass: no pressure total needed
+        PP_RET((inverse_x<float, double>(ex, INV_FINAL, (double*)p, false, pair)));
       }
     }
   }

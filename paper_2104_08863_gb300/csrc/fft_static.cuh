@@ -93,11 +93,11 @@ template <typename T> __host__ __device__ constexpr int padded_size(int n) { ret
 // One in-place stage.  Element n of transform t lives at buf[padi(t*BS + n*ES)]; B transforms.
 // MAPB: consecutive threads take consecutive transforms (column tiles) instead of
 // consecutive butterflies (rows).
-template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB>
+template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR>
 __device__ __forceinline__ void stage_inplace(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  constexpr Radix F = factorize(L, max_radix<T>());
+  constexpr Radix F = factorize(L, MAXR);
   constexpr int R = F.r[S];
-  constexpr int Ns = span_before(L, S, max_radix<T>());
+  constexpr int Ns = span_before(L, S, MAXR);
   constexpr int NBF = L / R;
   constexpr int TOTAL = NBF * B;
   constexpr int PER = (TOTAL + THREADS - 1) / THREADS;
@@ -139,20 +139,21 @@ __device__ __forceinline__ void stage_inplace(cplx<T>* buf, const cplx<T>* __res
   __syncthreads();
 }
 
-template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB>
+template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR>
 __device__ __forceinline__ void stages_from(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
-  constexpr Radix F = factorize(L, max_radix<T>());
+  constexpr Radix F = factorize(L, MAXR);
   if constexpr (S < F.n) {
-    stage_inplace<T, L, S, SIGN, B, THREADS, ES, BS, MAPB>(buf, tw);
-    stages_from<T, L, S + 1, SIGN, B, THREADS, ES, BS, MAPB>(buf, tw);
+    stage_inplace<T, L, S, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, tw);
+    stages_from<T, L, S + 1, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, tw);
   }
 }
 
-// Full transform, in place on buf (callers sync before: the first stage reads buf).
-template <typename T, int L, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB>
+// Full transform, in place on buf (callers sync before: the first stage reads buf).  MAXR caps
+// the radix (and so the values a thread stages per butterfly).
+template <typename T, int L, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR = max_radix<T>()>
 __device__ __forceinline__ void fft_static(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   static_assert(factorizable(L), "FFT length must be 2^a 3^b");
-  stages_from<T, L, 0, SIGN, B, THREADS, ES, BS, MAPB>(buf, tw);
+  stages_from<T, L, 0, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, tw);
 }
 
 }  // namespace pp

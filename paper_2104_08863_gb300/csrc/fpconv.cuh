@@ -8,8 +8,8 @@
 //    hi; the remaining 29 bits, converted by I2F and scaled by a power of two built in the
 //    exponent field, give lo, so hi + lo equals x to about 2^-47 relative.  Zeros, values below
 //    the FP32 normal range (flushed to zero) and values above it (to +-inf) are handled.
-//  * f32_pair_to_f64: a + b as a double, computed exactly in a 64-bit integer (the two
-//    significands aligned to the larger exponent) and rounded once to 53 bits.
+//  * f32_sum_to_f64: a + b as a double within one FP64 ulp: the FP32 sum and its exact TwoSum
+//    error are placed into one 53-bit significand with integer operations.
 //  * two_sum / two_diff (Knuth), two_prod (by FMA), df_add, df_mul: the classical
 //    double-float algorithms (Dekker 1971, Knuth TAOCP vol. 2), accurate to about 2^-47.
 // Everything is __host__ __device__ so that the host test suite can check it bit for bit.
@@ -47,13 +47,6 @@ __host__ __device__ __forceinline__ float float_of(uint32_t u) {
   memcpy(&x, &u, 4);
   return x;
 }
-__host__ __device__ __forceinline__ int clz64(uint64_t u) {
-#if defined(__CUDA_ARCH__)
-  return __clzll((long long)u);
-#else
-  return u ? __builtin_clzll(u) : 64;
-#endif
-}
 
 // x truncated toward zero to FP32 (flush below the normal range, +-inf above it).
 __host__ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
@@ -83,40 +76,34 @@ __host__ __device__ __forceinline__ void f64_split(double x, float& hi, float& l
   lo = (u >> 63) ? -mag : mag;
 }
 
-// a + b as a double, exact up to one final rounding to 53 bits (round half up on the
-// magnitude).  FP32 subnormals are treated as zero.
-__host__ __device__ __forceinline__ double f32_pair_to_f64(float a, float b) {
-  const uint32_t ua = bits_of(a), ub = bits_of(b);
-  const int ea = (int)((ua >> 23) & 0xff), eb = (int)((ub >> 23) & 0xff);
-  const bool za = ea == 0, zb = eb == 0;
-  if (za && zb) return 0.0;
-  if (zb || za) {   // one term is zero: widen the other exactly
-    const uint32_t v = zb ? ua : ub;
-    const int ev = zb ? ea : eb;
-    const uint64_t s = (uint64_t)(v >> 31) << 63;
-    return double_of(s | ((uint64_t)(ev + 896) << 52) | ((uint64_t)(v & 0x7fffffu) << 29));
+// a + b as a double, faithfully rounded (error below one FP64 ulp), by integer operations: the
+// FP32 sum s and its exact error e (TwoSum, |e| <= ulp(s)/2) are placed into one 53-bit
+// significand, s in the top 24 bits and e (aligned and truncated) in the low 29; a borrow from an
+// opposite-signed e renormalises by one bit.  FP32 subnormals are treated as zero.
+__host__ __device__ __forceinline__ double f32_sum_to_f64(float a, float b) {
+  const float s = a + b;
+  const float bp = s - a;
+  const float e = (a - (s - bp)) + (b - bp);
+  const uint32_t us = bits_of(s), ue = bits_of(e);
+  const uint32_t es = (us >> 23) & 0xffu, ee = (ue >> 23) & 0xffu;
+  if (es == 0u) return 0.0;
+  uint64_t R = (uint64_t)((us & 0x7fffffu) | 0x800000u) << 29;
+  int ex = (int)es + 896;   // FP64 biased exponent of s
+  if (ee != 0u) {
+    const uint32_t me = (ue & 0x7fffffu) | 0x800000u;
+    const int sh = (int)ee - (int)es + 29;   // <= 5
+    const uint32_t eu = sh >= 0 ? (me << sh) : (sh > -32 ? (me >> -sh) : 0u);
+    if ((us ^ ue) >> 31) {
+      R -= eu;
+      if (!(R >> 52)) {
+        R <<= 1;
+        --ex;
+      }
+    } else {
+      R += eu;
+    }
   }
-  const int E = ea > eb ? ea : eb;
-  // significands (with the implicit bit) in fixed point: leading bit of the larger at bit 61
-  const int sha = 38 - (E - ea), shb = 38 - (E - eb);
-  int64_t A = sha >= 0 ? (int64_t)((uint64_t)((ua & 0x7fffffu) | 0x800000u) << sha) : 0;
-  int64_t B = 0;
-  if (shb >= 0) B = (int64_t)((uint64_t)((ub & 0x7fffffu) | 0x800000u) << shb);
-  else if (shb > -24) B = (int64_t)(((ub & 0x7fffffu) | 0x800000u) >> (-shb));
-  if (ua >> 31) A = -A;
-  if (ub >> 31) B = -B;
-  const int64_t S = A + B;
-  if (S == 0) return 0.0;
-  const uint64_t sign = S < 0 ? (1ull << 63) : 0ull;
-  uint64_t U = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
-  const int lz = clz64(U);
-  U <<= lz;   // leading one at bit 63;  |a + b| = U * 2^(E - 188 - lz)
-  const uint64_t frac = (U >> 11) & 0xfffffffffffffull;
-  const uint64_t round = (U >> 10) & 1ull;
-  const int64_t dexp = (int64_t)E + 898 - lz;   // biased FP64 exponent of the leading one
-  if (dexp <= 0) return double_of(sign);
-  const uint64_t mag = ((uint64_t)dexp << 52) + frac + round;   // a carry rolls into the exponent
-  return double_of(sign | mag);
+  return double_of(((uint64_t)(us >> 31) << 63) | ((uint64_t)ex << 52) | (R & 0xfffffffffffffull));
 }
 
 // ---- double-float arithmetic (value = hi + lo) ----------------------------------------------

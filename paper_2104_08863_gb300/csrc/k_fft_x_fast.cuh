@@ -14,13 +14,14 @@
 namespace pp {
 
 template <typename T, int M> struct XTile {
-  static constexpr int E = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int E = 8;
+  static constexpr int MAXR = 8;
   static constexpr int LPB0 = (E * 256) / M;
   static constexpr int LPB = LPB0 < 1 ? 1 : (LPB0 > 64 ? 64 : LPB0);
   static constexpr int T0 = ((LPB * M / E) + 31) / 32 * 32;
   static constexpr int THREADS = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
   static constexpr int SMEM = padded_size<T>(LPB * M) * (int)sizeof(cplx<T>);
-  static constexpr int MINB = 2;
+  static constexpr int MINB = sizeof(T) == 4 ? 4 : 2;
 };
 
 template <typename T, typename TI, int M, int MODE>
@@ -49,15 +50,24 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
       }
     }
   } else {
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
+    // all of a thread's loads are issued before any shared-memory store
+    constexpr int PER = (LPB * M + THREADS - 1) / THREADS;
+    cplx<T> v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
       const int t = idx / M, n = idx % M;
       const int line = line0 + t;
-      buf[padi<T>(idx)] = line < nlines ? fwd_load<T, TI, MODE>(g, args, tt, tb, line, n) : mk<T>(T(0), T(0));
+      v[q] = (idx < LPB * M && line < nlines) ? fwd_load<T, TI, MODE>(g, args, tt, tb, line, n) : mk<T>(T(0), T(0));
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      if (idx < LPB * M) buf[padi<T>(idx)] = v[q];
     }
   }
   __syncthreads();
-  fft_static<T, M, -1, LPB, THREADS, 1, M, false>(buf, tt.tw_m);
+  fft_static<T, M, -1, LPB, THREADS, 1, M, false, C::MAXR>(buf, tt.tw_m);
   constexpr int M1 = M + 1;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
@@ -79,21 +89,58 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int line0 = blockIdx.x * LPB;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
-    const int t = idx / M, kx = idx % M;
-    const int line = line0 + t;
-    cplx<T> Z = mk<T>(T(0), T(0));
-    if (line < nlines) {
-      const cplx<T>* row = spec + (size_t)line * g.pitch;
-      Z = inv_pre(kx, ld_c(row + kx), ld_c(row + (M - kx)), ldg_c(tt.tw_post + kx));
+  {
+    constexpr int PER = (LPB * M + THREADS - 1) / THREADS;
+    cplx<T> Xk[PER], Xm[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      const int t = idx / M, kx = idx % M;
+      const int line = line0 + t;
+      Xk[q] = Xm[q] = mk<T>(T(0), T(0));
+      if (idx < LPB * M && line < nlines) {
+        const cplx<T>* row = spec + (size_t)line * g.pitch;
+        Xk[q] = ld_c(row + kx);
+        Xm[q] = ld_c(row + (M - kx));
+      }
     }
-    buf[padi<T>(idx)] = Z;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      const int kx = idx % M;
+      if (idx < LPB * M) buf[padi<T>(idx)] = inv_pre(kx, Xk[q], Xm[q], ldg_c(tt.tw_post + kx));
+    }
   }
   __syncthreads();
-  fft_static<T, M, 1, LPB, THREADS, 1, M, false>(buf, tt.tw_m);
+  fft_static<T, M, 1, LPB, THREADS, 1, M, false, C::MAXR>(buf, tt.tw_m);
   const T s = T(scl);
-  if constexpr (!ACC) {
+  if constexpr (!ACC && MODE == INV_FINAL) {
+    // refined pressure: the pair (hi, lo) of every element is loaded before any assembly
+    constexpr int PER = (LPB * M + THREADS - 1) / THREADS;
+    float2 h[PER], l[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      const int t = idx / M, n = idx % M;
+      const int line = line0 + t;
+      h[q] = l[q] = make_float2(0.f, 0.f);
+      if (idx < LPB * M && line < nlines) {
+        const size_t off = (size_t)line * g.nx + 2 * n;
+        h[q] = *reinterpret_cast<const float2*>(pair.hi + off);
+        if (pair.lo) l[q] = *reinterpret_cast<const float2*>(pair.lo + off);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      const int t = idx / M, n = idx % M;
+      const int line = line0 + t;
+      if (idx >= LPB * M || line >= nlines) continue;
+      const cplx<T> z = buf[padi<T>(idx)];
+      const size_t off = (size_t)line * g.nx + 2 * n;
+      final_store(out + off, h[q], l[q], float(z.x * s), float(z.y * s));
+    }
+  } else if constexpr (!ACC) {
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < LPB * M; idx += THREADS) {
       const int t = idx / M, n = idx % M;
@@ -112,7 +159,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
       const int line = line0 + t;
       if (line >= nlines) break;
       T hs = T(0), hc = T(0);
-#pragma unroll 4
+#pragma unroll 8
       for (int n = lane; n < M; n += 32) {
         const cplx<T> z = buf[padi<T>(t * M + n)];
         const T x0 = z.x * s, x1 = z.y * s;
@@ -197,8 +244,8 @@ cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<
       if (accumulate) PP_INVF(INV_STORE, true) else PP_INVF(INV_STORE, false)
     }
   } else {
-    if (mode != INV_FINAL || !accumulate) return cudaErrorNotSupported;
-    PP_INVF(INV_FINAL, true)
+    if (mode != INV_FINAL) return cudaErrorNotSupported;
+    if (accumulate) PP_INVF(INV_FINAL, true) else PP_INVF(INV_FINAL, false)
   }
 #undef PP_INVF
   return cudaGetLastError();

@@ -192,7 +192,7 @@ __device__ __forceinline__ cplx<T> inv_pre(int kx, cplx<T> Xk, cplx<T> Xm, cplx<
 }
 
 // Epilogue of the inverse x-transform: store, accumulate, or (INV_FINAL) assemble the FP64
-// pressure hi + (lo + v) of the refined solve exactly by integer arithmetic.
+// pressure hi + (lo + v) of the refined solve by integer arithmetic (faithful to one FP64 ulp).
 template <typename T, typename TO, int MODE>
 __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const PairArgs& pair) {
   if constexpr (MODE == INV_ACCUM) {
@@ -204,11 +204,16 @@ __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const P
       const float2 h = *reinterpret_cast<const float2*>(pair.hi + off);
       float2 l = make_float2(0.0f, 0.0f);
       if (pair.lo) l = *reinterpret_cast<const float2*>(pair.lo + off);
-      RealIO<TO>::store2(o, f32_pair_to_f64(h.x, l.x + x0), f32_pair_to_f64(h.y, l.y + x1));
+      RealIO<TO>::store2(o, f32_sum_to_f64(h.x, l.x + x0), f32_sum_to_f64(h.y, l.y + x1));
     }
   } else {
     RealIO<TO>::store2(o, TO(x0), TO(x1));
   }
+}
+
+// INV_FINAL epilogue on preloaded pairs: p = hi + (lo + v), v the last correction.
+__device__ __forceinline__ void final_store(double* o, float2 h, float2 l, float v0, float v1) {
+  RealIO<double>::store2(o, f32_sum_to_f64(h.x, l.x + v0), f32_sum_to_f64(h.y, l.y + v1));
 }
 
 // ---- per-line form of the refinement residual (specialised kernels) --------------------------
