@@ -31,10 +31,21 @@ __global__ void __launch_bounds__(ZTile<T, NZ>::THREADS, ZTile<T, NZ>::MINB) k_f
   const int kx0 = blockIdx.x * W;
   cplx<T>* plane = spec + (size_t)j * NZ * g.pitch + kx0;
   const int ncol = min(W, g.ncols - kx0);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < NZ * W; idx += THREADS) {
-    const int n = idx / W, c = idx % W;
-    buf[padi<T>(idx)] = c < ncol ? ld_c(plane + (size_t)n * g.pitch + c) : mk<T>(T(0), T(0));
+  {
+    // every load of the thread is issued before its first shared-memory store
+    constexpr int PER = (NZ * W + THREADS - 1) / THREADS;
+    cplx<T> v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      const int n = idx / W, c = idx % W;
+      v[q] = (idx < NZ * W && c < ncol) ? ld_c(plane + (size_t)n * g.pitch + c) : mk<T>(T(0), T(0));
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * THREADS;
+      if (idx < NZ * W) buf[padi<T>(idx)] = v[q];
+    }
   }
   __syncthreads();
   fft_static<T, NZ, SIGN, W, THREADS, W, 1, true>(buf, tt.tw_z);
