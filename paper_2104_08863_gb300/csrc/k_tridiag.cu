@@ -437,7 +437,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Per-mode LU of the reduced interface system, built once per plan in FP64 (RHS-independent).
-// For interface i (between blocks i and i+1) of system sys, entry k of table[(i*5 + k)*nsys + sys]:
+// For interface i (between blocks i and i+1) of system sys, entry k of
+// table[(sys*(P-1) + i)*5 + k] (one contiguous record per system):
 //   0: vL_i      the spike v of block i at its last row
 //   1: inv_i     1 / (1 - d01 d10),  d01 = -wL_i - vL_i wF_i X01_{i-1},  d10 = -vF_{i+1}
 //   2: X01_i     -d01 inv_i
@@ -484,12 +485,12 @@ __global__ void __launch_bounds__(128) k_reduced_setup(Geometry g, int P, int m,
     const double d01 = -wL0 - vL0 * wF0 * pX01, d10 = -vF1;
     const double inv = 1.0 / (1.0 - d01 * d10);
     const double X01 = -d01 * inv, X10 = -d10 * inv;
-    float* t = tab + (size_t)(i * 5) * nsys + sys;
+    float* t = tab + ((size_t)sys * (P - 1) + i) * 5;
     t[0] = float(vL0);
-    t[(size_t)nsys] = float(inv);
-    t[(size_t)2 * nsys] = float(X01);
-    t[(size_t)3 * nsys] = float(X10);
-    t[(size_t)4 * nsys] = i + 1 < P - 1 ? float(wF1) : 0.f;
+    t[1] = float(inv);
+    t[2] = float(X01);
+    t[3] = float(X10);
+    t[4] = i + 1 < P - 1 ? float(wF1) : 0.f;
     pX01 = X01;
     vF0 = vF1; vL0 = vL1; wF0 = wF1; wL0 = wL1;
   }
@@ -527,9 +528,9 @@ __global__ void __launch_bounds__(256, 2) k_tridiag_reg(Geometry g, int P, int S
 #pragma unroll 1
     for (int i = 0; i < M; ++i, src += rstride) cp_async8(&Xs[i * NT + tid], src);
   }
-  for (int q = tid; q < 5 * (P - 1) * S; q += NT) {   // the reduced-system table slice
-    const int ik = q / S, qs = q - ik * S;
-    if (sys0 + qs < nsys) cp_async4(&tsh[q], &rtab[(size_t)ik * nsys + sys0 + qs]);
+  for (int q = tid; q < 5 * (P - 1) * S; q += NT) {   // the reduced-system table slice, [i][k][s]
+    const int qs = q / (5 * (P - 1)), ik = q - qs * 5 * (P - 1);
+    if (sys0 + qs < nsys) cp_async4(&tsh[ik * S + qs], &rtab[(size_t)(sys0 + qs) * 5 * (P - 1) + ik]);
   }
   float rbv[M], gvv[M];
   if (active) {
@@ -614,6 +615,169 @@ __global__ void __launch_bounds__(256, 2) k_tridiag_reg(Geometry g, int P, int S
       *dst = xn;
       dst -= rstride;
     }
+  }
+}
+
+// ---- FP32 PDD with the reduced system solved by warp scans (P a power of two <= 32) ---------
+// Same blocks and factors as k_tridiag_reg, but threads are numbered system-major (tid = s*P + b),
+// so the P blocks of a system are P consecutive lanes of one warp and the reduced interface
+// system needs no shared memory and no barrier.  With the per-mode LU (vL, inv, X01, X10, tw) of
+// interface i, its two sweeps are first-order linear recurrences
+//   y0_i = (inv_i vL_i) y0_{i-1} + (inv_i xL_i + X01_i xF_{i+1}),
+//   z1_i = (tw_i inv_i) z1_{i+1} + y1_i,   y1_i = X10_i (xL_i + vL_i y0_{i-1}) + inv_i xF_{i+1},
+// solved by log2(P)-step inclusive scans of affine maps over the segment's lanes; then
+// z0_i = y0_i + tw_i X01_i z1_{i+1}, the neighbour values are alpha_b = z0_{b-1}, beta_b = z1_b.
+// The tile is staged through shared memory in both directions (coalesced copies of S-system row
+// segments), laid out [block][row][system] with an odd block stride so that a warp's lanes, which
+// walk different blocks of the same rows, fall on distinct bank pairs.
+
+// (A, B) <- (A, B) o (A', B') from the lane d below within segments of P lanes (inclusive scan)
+__device__ __forceinline__ void scan_up(int P, int lseg, float& A, float2& B) {
+  for (int d = 1; d < P; d <<= 1) {
+    const float Ap = __shfl_up_sync(0xffffffffu, A, d);
+    const float Bx = __shfl_up_sync(0xffffffffu, B.x, d), By = __shfl_up_sync(0xffffffffu, B.y, d);
+    if (lseg >= d) {
+      B = make_float2(fmaf(A, Bx, B.x), fmaf(A, By, B.y));
+      A *= Ap;
+    }
+  }
+}
+__device__ __forceinline__ void scan_down(int P, int lseg, float& A, float2& B) {
+  for (int d = 1; d < P; d <<= 1) {
+    const float Ap = __shfl_down_sync(0xffffffffu, A, d);
+    const float Bx = __shfl_down_sync(0xffffffffu, B.x, d), By = __shfl_down_sync(0xffffffffu, B.y, d);
+    if (lseg + d < P) {
+      B = make_float2(fmaf(A, Bx, B.x), fmaf(A, By, B.y));
+      A *= Ap;
+    }
+  }
+}
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int d) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) k_tridiag_scan(Geometry g, int P, int S, int low, const float* __restrict__ a,
+                                                         const float* __restrict__ c, const double* __restrict__ lamx,
+                                                         const double* __restrict__ lamz, const float* __restrict__ rtab,
+                                                         cplx<float>* __restrict__ spec) {
+  extern __shared__ __align__(16) float2 tile[];   // [b][i][s] with block stride BS, then a and c
+  const int NT = P * S;
+  const int BS = M * S + 1;
+  constexpr int MS = M | 1;                        // odd per-block stride of the coefficient copies
+  float* as = reinterpret_cast<float*>(tile + (size_t)P * BS);
+  float* csm = as + P * MS;
+  for (int j = threadIdx.x; j < g.ny; j += NT) {
+    const int bj = j / M, ij = j - bj * M;
+    as[bj * MS + ij] = a[j];
+    csm[bj * MS + ij] = c[j];
+  }
+  // a CTA owns the S systems kx0 .. kx0+S-1 of one kz; columns past the padded row (pitch) are
+  // not touched, columns in [ncols, pitch) are padding and go back unchanged
+  const int ntile = (g.ncols + S - 1) / S;
+  const int kz = blockIdx.x / ntile;
+  const int kx0 = (blockIdx.x - kz * ntile) * S;
+  const size_t rstride = (size_t)g.nz * g.pitch;
+  // ---- coalesced copy-in: thread t copies block t / S of system t % S (S-system row segments)
+  const int cpb = threadIdx.x / S, cps = threadIdx.x - cpb * S;
+  const bool cvalid = kx0 + cps < g.pitch;
+  const float2* gsrc = reinterpret_cast<const float2*>(spec) + (size_t)kz * g.pitch + kx0 + cps +
+                       (size_t)cpb * M * rstride;
+  float2* tsrc = tile + cpb * BS + cps;
+  if (cvalid) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) cp_async8(tsrc + i * S, gsrc + (size_t)i * rstride);
+  }
+  // ---- compute role: thread (s, b); its interface record is fetched while the tile lands
+  const int s = threadIdx.x / P, b = threadIdx.x - s * P;
+  const int lseg = b;
+  const int kx = kx0 + s;
+  const int sys = kz * g.ncols + kx;
+  const bool active = kx < g.ncols && !(kx == 0 && kz == 0) && !is_low(kx, kz, g.nz, low);
+  float vL = 0.f, inv = 0.f, X01 = 0.f, X10 = 0.f, tw = 0.f;
+  if (P > 1 && active && b < P - 1) {
+    const float* t = rtab + ((size_t)sys * (P - 1) + b) * 5;
+    vL = __ldg(t); inv = __ldg(t + 1); X01 = __ldg(t + 2); X10 = __ldg(t + 3); tw = __ldg(t + 4);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int r0 = b * M;
+  float2* blk = tile + b * BS + s;   // row i at blk[i * S]
+  const float* ab = as + b * MS;      // a_{r0 + i} at ab[i]
+  const float* cb = csm + b * MS;
+  float rbv[M], gvv[M];
+  float2 xF = make_float2(0.f, 0.f), xL = make_float2(0.f, 0.f);
+  if (active) {
+    const float sigma = float(-(lamx[kx] + lamz[kz]));
+    float e = ab[0] + sigma, gv = ab[0], rb = rcp_nr(cb[0] + e);
+    float run = 1.f;
+    float2 gg = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const float cj = cb[i];
+      const float2 F = blk[i * S];
+      float mult = 0.f;
+      if (i > 0) {
+        mult = ab[i] * rb;
+        e = fmaf(mult, e, sigma);
+        gv = mult * gv;
+        rb = rcp_nr(cj + e);
+      }
+      gg = make_float2(fmaf(mult, gg.x, -F.x), fmaf(mult, gg.y, -F.y));
+      blk[i * S] = gg;
+      rbv[i] = rb;
+      gvv[i] = gv;
+      const float kap = run * rb;
+      xF.x = fmaf(kap, gg.x, xF.x);
+      xF.y = fmaf(kap, gg.y, xF.y);
+      run *= cj * rb;
+    }
+    xL = make_float2(gg.x * rb, gg.y * rb);
+  }
+  float2 alpha = make_float2(0.f, 0.f), beta = make_float2(0.f, 0.f);
+  if (P > 1) {
+    // interface i = b (lanes b <= P-2); every lane takes part in the shuffles
+    const float2 xFn = shfl_down2(xF, 1);                 // xF_{i+1}
+    float A = inv * vL;
+    float2 B = make_float2(fmaf(inv, xL.x, X01 * xFn.x), fmaf(inv, xL.y, X01 * xFn.y));
+    scan_up(P, lseg, A, B);                               // B = y0_i
+    const float2 y0 = B;
+    float2 y0m = shfl_up2(y0, 1);                         // y0_{i-1}
+    if (lseg == 0) y0m = make_float2(0.f, 0.f);
+    const float2 q0 = make_float2(fmaf(vL, y0m.x, xL.x), fmaf(vL, y0m.y, xL.y));
+    float G = tw * inv;
+    float2 Y = make_float2(fmaf(X10, q0.x, inv * xFn.x), fmaf(X10, q0.y, inv * xFn.y));
+    if (lseg == P - 1) { G = 0.f; Y = make_float2(0.f, 0.f); }
+    scan_down(P, lseg, G, Y);                             // Y = z1_i
+    const float2 z1 = Y;
+    const float2 z1n = shfl_down2(z1, 1);                 // z1_{i+1}
+    const float a0 = tw * X01;
+    const float2 z0 = make_float2(fmaf(a0, z1n.x, y0.x), fmaf(a0, z1n.y, y0.y));
+    const float2 z0m = shfl_up2(z0, 1);                   // z0_{b-1}
+    if (lseg > 0) alpha = z0m;
+    if (lseg < P - 1) beta = z1;
+  }
+  if (active) {
+    float2 xn = beta;
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+      const float cj = cb[i];
+      const float2 G2 = blk[i * S];
+      const float tx = fmaf(cj, xn.x, fmaf(alpha.x, gvv[i], G2.x));
+      const float ty = fmaf(cj, xn.y, fmaf(alpha.y, gvv[i], G2.y));
+      xn = make_float2(tx * rbv[i], ty * rbv[i]);
+      blk[i * S] = xn;
+    }
+  }
+  __syncthreads();
+  // ---- coalesced copy-out
+  if (cvalid) {
+    float2* gdst = reinterpret_cast<float2*>(spec) + (size_t)kz * g.pitch + kx0 + cps + (size_t)cpb * M * rstride;
+#pragma unroll
+    for (int i = 0; i < M; ++i) gdst[(size_t)i * rstride] = tsrc[i * S];
   }
 }
 
@@ -808,6 +972,25 @@ cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int p
   if (!reg_tridiag_ok(g.ny, parts)) return cudaErrorNotSupported;
   const int m = g.ny / parts;
   const int S = reg_systems_per_cta(parts);
+  if (parts <= 32 && (parts & (parts - 1)) == 0) {   // warp-scan variant
+    const int nt = parts * S;
+    const size_t smem = (size_t)parts * (m * S + 1) * 8 + (size_t)2 * parts * (m | 1) * 4;
+    const int blocks = g.nz * ((g.ncols + S - 1) / S);
+#define PP_SCAN_CASE(MM)                                                                                       \
+  case MM: {                                                                                                   \
+    cudaError_t e = prep(k_tridiag_scan<MM>, smem);                                                            \
+    if (e != cudaSuccess) return e;                                                                            \
+    k_tridiag_scan<MM><<<blocks, nt, smem, st>>>(g, parts, S, low_modes, tb.f.a, tb.f.c, tb.lamx, tb.lamz,     \
+                                                 tb.red_f, spec);                                              \
+    return cudaGetLastError();                                                                                 \
+  }
+    switch (m) {
+      PP_SCAN_CASE(1) PP_SCAN_CASE(2) PP_SCAN_CASE(3) PP_SCAN_CASE(4) PP_SCAN_CASE(6) PP_SCAN_CASE(8)
+      PP_SCAN_CASE(12) PP_SCAN_CASE(16) PP_SCAN_CASE(24)
+      default: break;
+    }
+#undef PP_SCAN_CASE
+  }
   const int nt = parts * S;
   const size_t tabf = ((size_t)5 * (parts - 1) * S + 1) & ~(size_t)1;
   const size_t smem = (size_t)6 * nt * sizeof(float) + tabf * sizeof(float) + (size_t)m * 8 * nt;
