@@ -475,6 +475,9 @@ PROFILE_CASES = {
     # the 768-row wall-normal grid of the 1536x768x1024 precision form on a 256x256 plane
     "fp32_refined_solve_256x768x256": (W.ChannelCase("channel_256x768x256_tanh2.2", 256, 768, 256, 2.2), 2, 1,
                                        "solve"),
+    # the 1536-point x lines of the 1536x768x1024 precision form on a 96x128 (y, z) section
+    "fp32_refined_solve_1536x96x128": (W.ChannelCase("channel_1536x96x128_tanh2.2", 1536, 96, 128, 2.2), 2, 1,
+                                       "solve"),
 }
 
 
