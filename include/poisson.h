@@ -6,7 +6,7 @@
  * wall-bounded and stretched in y, it solves the discrete Poisson equation of Eq. 8 by
  * real FFTs in x and z (Eq. 9), one wall-normal tridiagonal system per (kx, kz) solved by
  * the PDD algorithm of Sec. 2.2 (Eqs. 10-21, exact reduced system) or by Thomas, and the
- * inverse FFTs (steps (1)-(8) of Sec. 3.1).  The divergence of Eq. 7 and the velocity
+ * inverse FFTs (steps (1)-(8) of Sec. 3.2).  The divergence of Eq. 7 and the velocity
  * correction of Eq. 4 are fused around the solve.
  *
  * Conventions (all fields C-ordered, x fastest, contiguous, 16-byte aligned device memory):

@@ -27,7 +27,7 @@ Readings of the paper (the text is silent or garbled on these points):
 * cell centres in y are midpoints of the adjacent faces;
 * the singular (kx, kz) = (0, 0) mode is made compatible by removing the volume-weighted
   mean of f and is gauged by a zero volume-weighted mean of p;
-* steps (6) and (8) of Sec. 3.1 are inverse transforms;
+* steps (6) and (8) of Sec. 3.2 are inverse transforms;
 * advection is the divergence form with arithmetic two-point face averages, the no-slip wall
   enters the diffusion through the wall value 0 half a cell from the first node, and the flow is
   driven by a constant streamwise body force.

@@ -4,7 +4,7 @@
 // stretched-grid metrics (Sec. 2; cell heights dy_j, centre distances h_j, the wall-normal
 // coefficients a_j = 1/(dy_j h_j), c_j = 1/(dy_j h_{j+1})), the modified wavenumbers of
 // Eq. 9 (lambda = -(4/d^2) sin^2(pi k / N)), the FFT factorisations and twiddles.  The solve
-// entry points run the pipeline of Sec. 3.1 steps (1)-(8) as a sequence of kernels on the
+// entry points run the pipeline of Sec. 3.2 steps (1)-(8) as a sequence of kernels on the
 // caller's stream.
 #include <math.h>
 #include <stdlib.h>

@@ -1,4 +1,4 @@
-// Transform kernels of the pressure solve (Eq. 9; steps (2), (4), (6), (8) of Sec. 3.1).
+// Transform kernels of the pressure solve (Eq. 9; steps (2), (4), (6), (8) of Sec. 3.2).
 //
 //  k_fwd_x : per x-line (j, k), Nx real values -> Nx/2+1 complex (e^{-2 pi i kx x / Nx}).
 //            The real line is packed as Nx/2 complex values, transformed by the Stockham

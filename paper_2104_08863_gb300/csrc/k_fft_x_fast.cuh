@@ -1,4 +1,4 @@
-// Specialised x-transform kernels (steps (2) and (8) of Sec. 3.1) for the half-lengths
+// Specialised x-transform kernels (steps (2) and (8) of Sec. 3.2) for the half-lengths
 // M = Nx/2 in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024}.
 //
 // A CTA takes LPB consecutive x-lines, which are one contiguous stretch of the field, packs

@@ -1,4 +1,4 @@
-// Specialised z-transform kernel (step (4) / (6) of Sec. 3.1): a CTA transforms a tile of W
+// Specialised z-transform kernel (step (4) / (6) of Sec. 3.2): a CTA transforms a tile of W
 // adjacent kx columns of one y-plane along z (Nz points each).  The tile is loaded with
 // coalesced row segments of W complex values, transformed in place in (padded) shared memory
 // by the compile-time Stockham engine, and stored back.  W and the thread count are chosen so
