@@ -172,8 +172,16 @@ def measured_peaks():
 FWD_X_FP64_TRAFFIC = {"bytes": 3.05e9, "ncu_fp64_pipe_active_pct": 85.9,
                       "source": "ncu capture at 256x192x256 scaled x8 by points"}
 
-# DRAM traffic of other kernels from ncu captures (per launch at the bench size), when taken.
-KERNEL_TRAFFIC = {}
+# DRAM traffic of the momentum stages from an ncu capture of the same kernels on the 256x192x256
+# timestep (profiles/momentum_fp64_timestep_256x192x256.md), scaled by the number of points (x 8.0)
+# to the 512x384x512 launches; the capture shows the FP64 pipe 89 % busy.  Valid for the kernel as
+# captured.
+KERNEL_TRAFFIC = {
+    "momentum_1": {"bytes": 4.58e9, "ncu_fp64_pipe_active_pct": 88.9,
+                   "source": "ncu capture at 256x192x256 scaled x8 by points"},
+    "momentum_2": {"bytes": 7.00e9, "ncu_fp64_pipe_active_pct": 89.1,
+                   "source": "ncu capture at 256x192x256 scaled x8 by points"},
+}
 
 # FP64 FMA throughput measured on this machine's GB300 by a DFMA-throughput microbenchmark:
 # 502 G DFMA/s (1.6 per clock per SM at the 2070 MHz nominal clock) = 1004 GFLOP/s.
