@@ -351,6 +351,7 @@ def run_gpu(args):
     d2h = h2d + 8 * CASE.npoints
 
     forms = precision_forms(dev) if (world == 1 and not args.no_forms) else None
+    ts_forms = timestep_forms(dev) if (world == 1 and not args.no_forms) else None
     cpu = oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -360,10 +361,62 @@ def run_gpu(args):
                "cpu_baseline": cpu,
                "e2e": {"value": world * CASE.npoints / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-               "gpu_launches": launches_per_step * args.steps, "clocks": clk, "precision_forms": forms}
+               "gpu_launches": launches_per_step * args.steps, "clocks": clk, "precision_forms": forms,
+               "timestep_forms": ts_forms}
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def timestep_forms(dev, steps: int = 5, warmup: int = 3):
+    """The bench timestep in FP64 and in the FP32-refined form (double-float momentum and
+    divergence on FP32 pairs, two-correction Poisson solve) on the 512 x 384 x 512 channel.
+
+    Both start from the bench's initial state; after one timestep the refined form's velocity and
+    pressure are compared with the FP64 form's (max |difference| / max |FP64|).  Each form is
+    then timed over `steps` further timesteps with CUDA events.
+    """
+    import torch
+    import paper_2104_08863_gb300 as P
+    faces = W.tanh_faces(CASE.ny, CASE.stretch)
+    u0, v0, w0 = W.poiseuille_plus_noise(1, CASE)
+    out = {"workload": f"{CASE.name} full timestep from the bench's initial state"}
+    ref = None
+    for name, prec in (("fp64", P.PP_FP64), ("fp32_refined", P.PP_FP32_REFINED)):
+        kw = dict(tridiag=P.PT_PDD_EXACT, pdd_parts=PDD_PARTS) if prec == P.PP_FP64 else dict(refine_steps=2)
+        plan = P.Plan(CASE.nx, CASE.ny, CASE.nz, faces, CASE.lx, CASE.lz, precision=prec, flags=P.POISSON_TIMING,
+                      device=dev, **kw)
+        u, v, w = (torch.from_numpy(a).to(dev) for a in (u0, v0, w0))
+        p = torch.empty(CASE.ny, CASE.nz, CASE.nx, dtype=torch.float64, device=dev)
+        scratch = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        plan.timestep(u, v, w, DT, NU, FX, p_out=p, scratch=scratch)
+        snap = [t.clone() for t in (u, v, w, p)]
+        for _ in range(warmup):
+            plan.timestep(u, v, w, DT, NU, FX, p_out=p, scratch=scratch)
+        stream = torch.cuda.current_stream(dev)
+        stage = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.timestep(u, v, w, DT, NU, FX, p_out=p, scratch=scratch)
+            for k, ms in plan.stage_times():
+                stage[k] = stage.get(k, 0.0) + ms
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        entry = {"ms_per_timestep": ms, "gpts_s": CASE.npoints / (ms * 1e-3) / 1e9,
+                 "stage_ms": {k: round(x / steps, 4) for k, x in sorted(stage.items(), key=lambda kv: -kv[1])}}
+        if ref is None:
+            ref = snap
+        else:
+            vel = max(float((a - b).abs().max()) / float(b.abs().max()) for a, b in zip(snap[:3], ref[:3]))
+            entry["maxrel_velocity_vs_fp64"] = vel
+            entry["maxrel_pressure_vs_fp64"] = float((snap[3] - ref[3]).abs().max()) / float(ref[3].abs().max())
+        out[name] = entry
+        del plan, u, v, w, p, scratch, snap
+        torch.cuda.empty_cache()
+    return out
 
 
 def precision_forms(dev, steps: int = 5, warmup: int = 3):
@@ -552,7 +605,8 @@ def main():
         import torch
         from paper_2104_08863_gb300 import build as b
         b.build()
-        print(json.dumps(precision_forms(torch.device("cuda", 0))))
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"precision_forms": precision_forms(dev), "timestep_forms": timestep_forms(dev)}))
     else:
         run_gpu(args)
 

@@ -552,7 +552,24 @@ poisson_status check_timestep_args(const poisson_plan_s* pl, const void* u, cons
     for (int b = 0; b < a; ++b)
       if (all[a] && all[a] == all[b]) return PS_EINVAL;   // every buffer distinct
   }
-  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  return PS_OK;
+}
+
+// The predictor of PP_FP32_REFINED plans: u, v, w converted in place to FP32 pairs, the two Heun
+// stages in double-float; u, v, w hold u_star as pairs on return.
+poisson_status predictor_pairs(Exec& ex, void* u, void* v, void* w, void* ub, void* vb, void* wb, double dt,
+                               double nu, double fx) {
+  const poisson_plan_s* pl = ex.pl;
+  PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)u, cell_count(pl), ex.st));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)v, vface_count(pl), ex.st));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)w, cell_count(pl), ex.st));
+  MomArgsDF s1{(const float2*)u, (const float2*)v, (const float2*)w, nullptr, nullptr, nullptr,
+               (float2*)ub, (float2*)vb, (float2*)wb, 0.0, 1.0, dt, nu, fx};
+  PP_TRY_N("momentum_df_1", launch_momentum_df(pl->g, ex.dt, s1, ex.st));
+  MomArgsDF s2{(const float2*)ub, (const float2*)vb, (const float2*)wb, (const float2*)u, (const float2*)v,
+               (const float2*)w, (float2*)u, (float2*)v, (float2*)w, 0.5, 0.5, 0.5 * dt, nu, fx};
+  PP_TRY_N("momentum_df_2", launch_momentum_df(pl->g, ex.dt, s2, ex.st));
   return PS_OK;
 }
 
@@ -628,7 +645,12 @@ poisson_status momentum_predictor(poisson_plan_t pl, void* u, void* v, void* w, 
   pl->launches = 0;
   pl->nev = 0;
   Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
-  return predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx);
+  if (pl->precision != PP_FP32_REFINED) return predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx);
+  PP_RET(predictor_pairs(ex, u, v, w, ub, vb, wb, dt, nu, fx));
+  PP_TRY_N("from_pairs", launch_from_pairs((double*)u, cell_count(pl), ex.st));
+  PP_TRY_N("from_pairs", launch_from_pairs((double*)v, vface_count(pl), ex.st));
+  PP_TRY_N("from_pairs", launch_from_pairs((double*)w, cell_count(pl), ex.st));
+  return PS_OK;
 }
 
 poisson_status projection_timestep(poisson_plan_t pl, void* u, void* v, void* w, void* ub, void* vb, void* wb,
@@ -637,8 +659,20 @@ poisson_status projection_timestep(poisson_plan_t pl, void* u, void* v, void* w,
   pl->launches = 0;
   pl->nev = 0;
   Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
-  PP_RET(predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx));
-  return projection_impl(ex, u, v, w, p_out, dt);
+  if (pl->precision != PP_FP32_REFINED) {
+    PP_RET(predictor_impl(ex, u, v, w, ub, vb, wb, dt, nu, fx));
+    return projection_impl(ex, u, v, w, p_out, dt);
+  }
+  // refined: u_star as pairs; f = D(u_star)/dt into ub (FP64); the refined solve into p_out or
+  // vb; then the FP64 correction u = u_star - dt G p written over the pairs
+  PP_RET(predictor_pairs(ex, u, v, w, ub, vb, wb, dt, nu, fx));
+  double* f = (double*)ub;
+  double* p = p_out ? (double*)p_out : (double*)vb;
+  PP_TRY_N("divergence_df", launch_divergence_df(pl->g, ex.dt, (const float2*)u, (const float2*)v,
+                                                 (const float2*)w, dt, f, ex.st));
+  PP_RET(solve_impl(ex, f, p));
+  PP_TRY_N("gradient_pairs", launch_gradient_pairs(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, ex.st));
+  return PS_OK;
 }
 
 poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, void* gw, void* stream) {
@@ -696,7 +730,7 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   if (p_h && !p_d) return PS_EINVAL;
   PP_RET(check_timestep_args(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx));
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t es = pl->precision == PP_FP64 ? 8 : 4;
+  const size_t es = pl->precision == PP_FP32 ? 4 : 8;
   const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
   if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;

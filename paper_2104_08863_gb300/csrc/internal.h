@@ -189,6 +189,22 @@ template <typename T> struct MomArgs {
 template <typename T>
 cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st);
 
+// The FP64-accurate timestep on FP32 units (csrc/k_refined_ts.cu): the state as FP32 pairs
+// (hi, lo) in the FP64 buffers, double-float momentum stages, divergence and gradient.
+struct MomArgsDF {
+  const float2 *su, *sv, *sw;
+  const float2 *bu, *bv, *bw;
+  float2 *ou, *ov, *ow;
+  double alpha, beta, bdt, nu, fx;
+};
+cudaError_t launch_to_pairs(double* x, size_t n, cudaStream_t st);
+cudaError_t launch_from_pairs(double* x, size_t n, cudaStream_t st);
+cudaError_t launch_momentum_df(const Geometry& g, const DevTables& tb, const MomArgsDF& a, cudaStream_t st);
+cudaError_t launch_divergence_df(const Geometry& g, const DevTables& tb, const float2* u, const float2* v,
+                                 const float2* w, double dt, double* f, cudaStream_t st);
+cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const double* p, double* u, double* v,
+                                  double* w, double dt, cudaStream_t st);
+
 }  // namespace pp
 
 // Host plan (opaque to callers of include/poisson.h).

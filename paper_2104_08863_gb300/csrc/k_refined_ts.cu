@@ -1,0 +1,311 @@
+// The FP64-accurate timestep on FP32 units (the refined form of the projection timestep).
+//
+// The state (u, v, w) is carried through the step as FP32 pairs (hi, lo) with hi + lo equal to
+// the FP64 value to about 2^-47 (same bytes as FP64), and every per-point operation runs in
+// double-float arithmetic on the FP32 pipes (GB300 issues ~2 FP64 instructions per clock per SM
+// against 128 FP32):
+//   k_to_pairs        FP64 field -> pairs, in place (integer split, no FP64 instruction), and
+//   k_from_pairs      back (faithful integer assembly);
+//   k_momentum_df     one Heun stage (Eqs. 5-6) of the momentum right-hand side, the same
+//                     central differences and edge-flux sharing as k_momentum, in double-float;
+//   k_divergence_df   f = D(u*)/dt (Eq. 7) from the pairs, assembled as FP64 for the refined
+//                     Poisson solve;
+//   k_gradient_pairs  u = u* - dt G p (Eq. 4) from the pairs and the FP64 pressure, FP64 out.
+#include "fpconv.cuh"
+#include "internal.h"
+
+namespace pp {
+
+namespace {
+
+__device__ __forceinline__ df dadd(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df dsub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df dmul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df dfma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ df dtwice(df a) { return df{2.f * a.hi, 2.f * a.lo}; }
+__device__ __forceinline__ df ldp(const float2* p) {
+  const float2 v = __ldg(p);
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ df split(double x) {
+  df r;
+  f64_split(x, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ float2 f2(df a) { return make_float2(a.hi, a.lo); }
+
+constexpr int MTX = 32, MTZ = 8;
+
+struct RowCoefDF {
+  df c0, ca, cc, cay;
+  df v0, va, vc, vay;
+};
+
+__global__ void __launch_bounds__(256) k_to_pairs(double* __restrict__ x, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const df s = split(x[i]);
+    reinterpret_cast<float2*>(x)[i] = f2(s);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_from_pairs(double* __restrict__ x, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = reinterpret_cast<const float2*>(x)[i];
+    x[i] = f32_sum_to_f64(v.x, v.y);
+  }
+}
+
+// out = alpha * base + beta * s + bdt * R(s) on pairs (see k_momentum for the stencil).
+__global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF a, const double* __restrict__ inv_dy,
+                                                          const double* __restrict__ inv_h,
+                                                          const double* __restrict__ lo,
+                                                          const double* __restrict__ up, int jc) {
+  extern __shared__ unsigned char smem_raw[];
+  RowCoefDF* rc = reinterpret_cast<RowCoefDF*>(smem_raw);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int j0 = blockIdx.z * jc;
+  const int j1 = min(ny, j0 + jc);
+  const double bdtnu = a.bdt * a.nu;
+  const double cdx = bdtnu / (g.dx * g.dx), cdz = bdtnu / (g.dz * g.dz);
+  for (int r = threadIdx.y * MTX + threadIdx.x; r < j1 - j0; r += MTX * MTZ) {
+    const int j = j0 + r;
+    RowCoefDF c;
+    const double A = j > 0 ? lo[j] : 2.0 * inv_dy[0] * inv_dy[0];
+    const double C = j < ny - 1 ? up[j] : 2.0 * inv_dy[ny - 1] * inv_dy[ny - 1];
+    c.c0 = split(a.beta - 2.0 * cdx - 2.0 * cdz - bdtnu * (A + C));
+    c.ca = split(j > 0 ? bdtnu * lo[j] : 0.0);
+    c.cc = split(j < ny - 1 ? bdtnu * up[j] : 0.0);
+    c.cay = split(-0.25 * a.bdt * inv_dy[j]);
+    if (j >= 1) {
+      const double va = bdtnu * inv_h[j] * inv_dy[j - 1], vc = bdtnu * inv_h[j] * inv_dy[j];
+      c.v0 = split(a.beta - 2.0 * cdx - 2.0 * cdz - va - vc);
+      c.va = split(va);
+      c.vc = split(vc);
+      c.vay = split(-0.25 * a.bdt * inv_h[j]);
+    } else {
+      c.v0 = c.va = c.vc = c.vay = df{0.f, 0.f};
+    }
+    rc[r] = c;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * MTX + threadIdx.x;
+  const int k = blockIdx.y * MTZ + threadIdx.y;
+  if (i >= nx || k >= nz) return;
+  const df cDx = split(cdx), cDz = split(cdz);
+  const df cAx = split(-0.25 * a.bdt / g.dx), cAz = split(-0.25 * a.bdt / g.dz);
+  const df fterm = split(a.bdt * a.fx);
+  const df alpha = split(a.alpha);
+  const bool has_base = a.bu != nullptr;
+  const size_t plane = (size_t)nz * nx;
+  const int im = i == 0 ? nx - 1 : i - 1, ip = i == nx - 1 ? 0 : i + 1;
+  const int km = k == 0 ? nz - 1 : k - 1, kp = k == nz - 1 ? 0 : k + 1;
+  const size_t oc = (size_t)k * nx + i, oxm = (size_t)k * nx + im, oxp = (size_t)k * nx + ip;
+  const size_t ozm = (size_t)km * nx + i, ozp = (size_t)kp * nx + i;
+  const size_t ozm_xp = (size_t)km * nx + ip, ozp_xm = (size_t)kp * nx + im;
+  const float2* su = a.su;
+  const float2* sv = a.sv;
+  const float2* sw = a.sw;
+  const df zero{0.f, 0.f};
+
+  df u_m = zero, w_m = zero;
+  df u_c = ldp(su + (size_t)j0 * plane + oc), w_c = ldp(sw + (size_t)j0 * plane + oc);
+  df v_m = j0 > 0 ? ldp(sv + (size_t)(j0 - 1) * plane + oc) : zero;
+  df v_c = ldp(sv + (size_t)j0 * plane + oc);
+  df u_m_xp = zero, w_m_zp = zero;
+  df e_uv = zero, e_vw = zero;
+  if (j0 > 0) {
+    const size_t pm = (size_t)(j0 - 1) * plane, pc = (size_t)j0 * plane;
+    u_m = ldp(su + pm + oc);
+    w_m = ldp(sw + pm + oc);
+    u_m_xp = ldp(su + pm + oxp);
+    w_m_zp = ldp(sw + pm + ozp);
+    e_uv = dmul(dadd(ldp(sv + pc + oxm), v_c), dadd(u_m, u_c));
+    e_vw = dmul(dadd(ldp(sv + pc + ozm), v_c), dadd(w_m, w_c));
+  }
+  df vs_m = dadd(v_m, v_c);
+  if (j0 == 0) a.ov[oc] = has_base ? a.bv[oc] : f2(v_c);
+  for (int j = j0; j < j1; ++j) {
+    const RowCoefDF c = rc[j - j0];
+    const size_t pc = (size_t)j * plane, pn = pc + plane;
+    const bool top = j + 1 < ny;
+    const df u_n = top ? ldp(su + pn + oc) : zero;
+    const df w_n = top ? ldp(sw + pn + oc) : zero;
+    const df v_n = ldp(sv + pn + oc);
+    const df u_xm = ldp(su + pc + oxm), u_xp = ldp(su + pc + oxp), u_zm = ldp(su + pc + ozm), u_zp = ldp(su + pc + ozp);
+    const df u_zm_xp = ldp(su + pc + ozm_xp);
+    const df w_xm = ldp(sw + pc + oxm), w_xp = ldp(sw + pc + oxp), w_zm = ldp(sw + pc + ozm), w_zp = ldp(sw + pc + ozp);
+    const df w_zp_xm = ldp(sw + pc + ozp_xm);
+    const df v_xm = ldp(sv + pc + oxm), v_xp = ldp(sv + pc + oxp), v_zm = ldp(sv + pc + ozm), v_zp = ldp(sv + pc + ozp);
+    const df e_uv_n = top ? dmul(dadd(ldp(sv + pn + oxm), v_n), dadd(u_c, u_n)) : zero;
+    const df e_vw_n = top ? dmul(dadd(ldp(sv + pn + ozm), v_n), dadd(w_c, w_n)) : zero;
+    const df e_uw = dmul(dadd(w_xm, w_c), dadd(u_zm, u_c));
+    {   // u
+      df acc = fterm;
+      if (has_base) {
+        const float2 b = a.bu[pc + oc];
+        acc = dfma(alpha, df{b.x, b.y}, acc);
+      }
+      acc = dfma(c.c0, u_c, acc);
+      const df sx = dadd(u_xp, u_xm);
+      acc = dfma(cDx, sx, acc);
+      acc = dfma(cAx, dmul(dsub(u_xp, u_xm), dadd(sx, dtwice(u_c))), acc);
+      acc = dfma(cDz, dadd(u_zp, u_zm), acc);
+      acc = dfma(cAz, dsub(dmul(dadd(w_zp_xm, w_zp), dadd(u_c, u_zp)), e_uw), acc);
+      acc = dfma(c.cay, dsub(e_uv_n, e_uv), acc);
+      acc = dfma(c.ca, u_m, acc);
+      acc = dfma(c.cc, u_n, acc);
+      a.ou[pc + oc] = f2(acc);
+    }
+    {   // w
+      df acc = zero;
+      if (has_base) {
+        const float2 b = a.bw[pc + oc];
+        acc = dmul(alpha, df{b.x, b.y});
+      }
+      acc = dfma(c.c0, w_c, acc);
+      const df sz = dadd(w_zp, w_zm);
+      acc = dfma(cDz, sz, acc);
+      acc = dfma(cAz, dmul(dsub(w_zp, w_zm), dadd(sz, dtwice(w_c))), acc);
+      acc = dfma(cDx, dadd(w_xp, w_xm), acc);
+      acc = dfma(cAx, dsub(dmul(dadd(w_c, w_xp), dadd(u_zm_xp, u_xp)), e_uw), acc);
+      acc = dfma(c.cay, dsub(e_vw_n, e_vw), acc);
+      acc = dfma(c.ca, w_m, acc);
+      acc = dfma(c.cc, w_n, acc);
+      a.ow[pc + oc] = f2(acc);
+    }
+    if (j >= 1) {   // v at face j
+      df acc = zero;
+      if (has_base) {
+        const float2 b = a.bv[pc + oc];
+        acc = dmul(alpha, df{b.x, b.y});
+      }
+      acc = dfma(c.v0, v_c, acc);
+      const df vs = dadd(v_c, v_n);
+      acc = dfma(c.vay, dmul(dsub(vs, vs_m), dadd(vs, vs_m)), acc);
+      acc = dfma(cDx, dadd(v_xp, v_xm), acc);
+      acc = dfma(cAx, dsub(dmul(dadd(v_c, v_xp), dadd(u_m_xp, u_xp)), e_uv), acc);
+      acc = dfma(cDz, dadd(v_zp, v_zm), acc);
+      acc = dfma(cAz, dsub(dmul(dadd(v_c, v_zp), dadd(w_m_zp, w_zp)), e_vw), acc);
+      acc = dfma(c.va, v_m, acc);
+      acc = dfma(c.vc, v_n, acc);
+      a.ov[pc + oc] = f2(acc);
+    }
+    vs_m = dadd(v_c, v_n);
+    u_m = u_c; u_c = u_n;
+    w_m = w_c; w_c = w_n;
+    v_m = v_c; v_c = v_n;
+    u_m_xp = u_xp;
+    w_m_zp = w_zp;
+    e_uv = e_uv_n;
+    e_vw = e_vw_n;
+  }
+  if (j1 == ny) {
+    const size_t pw = (size_t)ny * plane + oc;
+    a.ov[pw] = has_base ? a.bv[pw] : __ldg(sv + pw);
+  }
+}
+
+// f = D(u*) / dt at every cell from the pairs, written as FP64 (faithful assembly).
+__global__ void __launch_bounds__(256) k_divergence_df(Geometry g, const float2* __restrict__ u,
+                                                      const float2* __restrict__ v, const float2* __restrict__ w,
+                                                      const double* __restrict__ inv_dy, double inv_dt,
+                                                      double* __restrict__ f) {
+  const size_t plane = (size_t)g.nz * g.nx;
+  const size_t total = (size_t)g.ny * plane;
+  const df cx = split(inv_dt / g.dx), cz = split(inv_dt / g.dz);
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const size_t r = idx - (size_t)j * plane;
+    const int k = (int)(r / g.nx);
+    const int i = (int)(r - (size_t)k * g.nx);
+    const size_t oxp = idx - i + (i + 1 == g.nx ? 0 : i + 1);
+    const size_t ozp = (size_t)j * plane + (size_t)(k + 1 == g.nz ? 0 : k + 1) * g.nx + i;
+    const df cy = split(inv_dt * inv_dy[j]);
+    df s = dmul(cx, dsub(ldp(u + oxp), ldp(u + idx)));
+    s = dfma(cz, dsub(ldp(w + ozp), ldp(w + idx)), s);
+    s = dfma(cy, dsub(ldp(v + idx + plane), ldp(v + idx)), s);
+    f[idx] = f32_sum_to_f64(s.hi, s.lo);
+  }
+}
+
+// u = u* - dt G p (Eq. 4): u* as pairs, p in FP64, result in FP64 (v's walls copied).
+__global__ void __launch_bounds__(256) k_gradient_pairs(Geometry g, const double* __restrict__ p, double* __restrict__ u,
+                                                        double* __restrict__ v, double* __restrict__ w,
+                                                        const double* __restrict__ inv_h, double dt) {
+  const size_t plane = (size_t)g.nz * g.nx;
+  const size_t total = (size_t)(g.ny + 1) * plane;
+  const double cx = dt / g.dx, cz = dt / g.dz;
+  const float2* up = reinterpret_cast<const float2*>(u);
+  const float2* vp = reinterpret_cast<const float2*>(v);
+  const float2* wp = reinterpret_cast<const float2*>(w);
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / plane);
+    const size_t r = idx - (size_t)j * plane;
+    const int k = (int)(r / g.nx);
+    const int i = (int)(r - (size_t)k * g.nx);
+    const float2 vv = vp[idx];
+    double vn = f32_sum_to_f64(vv.x, vv.y);
+    if (j < g.ny) {
+      const float2 uu = up[idx], ww = wp[idx];
+      const double pc = p[idx];
+      const double pxm = p[idx - i + (i == 0 ? g.nx - 1 : i - 1)];
+      const double pzm = p[(size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i];
+      u[idx] = f32_sum_to_f64(uu.x, uu.y) - cx * (pc - pxm);
+      w[idx] = f32_sum_to_f64(ww.x, ww.y) - cz * (pc - pzm);
+      if (j >= 1) vn -= dt * inv_h[j] * (pc - p[idx - plane]);
+    }
+    v[idx] = vn;
+  }
+}
+
+int grid_for(size_t total) {
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = 152 * 16;
+  return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_to_pairs(double* x, size_t n, cudaStream_t st) {
+  k_to_pairs<<<grid_for(n), 256, 0, st>>>(x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_pairs(double* x, size_t n, cudaStream_t st) {
+  k_from_pairs<<<grid_for(n), 256, 0, st>>>(x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_momentum_df(const Geometry& g, const DevTables& tb, const MomArgsDF& a, cudaStream_t st) {
+  const int tx = (g.nx + MTX - 1) / MTX, tz = (g.nz + MTZ - 1) / MTZ;
+  const long long tiles = (long long)tx * tz;
+  int chunks = (int)((3LL * 2 * 152 + tiles - 1) / tiles);
+  if (chunks > g.ny / 16) chunks = g.ny / 16;
+  if (chunks < 1) chunks = 1;
+  const int jc = (g.ny + chunks - 1) / chunks;
+  chunks = (g.ny + jc - 1) / jc;
+  const size_t smem = sizeof(RowCoefDF) * (size_t)jc;
+  const cudaError_t e = ensure_smem_limit((const void*)k_momentum_df, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tx, tz, chunks), block(MTX, MTZ);
+  k_momentum_df<<<grid, block, smem, st>>>(g, a, tb.d.inv_dy, tb.d.inv_h, tb.d.a, tb.d.c, jc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_divergence_df(const Geometry& g, const DevTables& tb, const float2* u, const float2* v,
+                                 const float2* w, double dt, double* f, cudaStream_t st) {
+  const size_t total = (size_t)g.ny * g.nz * g.nx;
+  k_divergence_df<<<grid_for(total), 256, 0, st>>>(g, u, v, w, tb.d.inv_dy, 1.0 / dt, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const double* p, double* u, double* v,
+                                  double* w, double dt, cudaStream_t st) {
+  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
+  k_gradient_pairs<<<grid_for(total), 256, 0, st>>>(g, p, u, v, w, tb.d.inv_h, dt);
+  return cudaGetLastError();
+}
+
+}  // namespace pp
