@@ -352,6 +352,7 @@ def run_gpu(args):
 
     forms = precision_forms(dev) if (world == 1 and not args.no_forms) else None
     ts_forms = timestep_forms(dev) if (world == 1 and not args.no_forms) else None
+    batch = batch_form(dev) if (world == 1 and not args.no_forms) else None
     cpu = oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -362,7 +363,7 @@ def run_gpu(args):
                "e2e": {"value": world * CASE.npoints / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "precision_forms": forms,
-               "timestep_forms": ts_forms}
+               "timestep_forms": ts_forms, "batch_form": batch}
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
