@@ -530,6 +530,7 @@ PROFILE_CASES = {
     # name: (case, precision, refine_steps, kind) with kind "timestep", "projection" or "solve"
     "fp64_timestep_256": (W.CHANNEL_256, 0, 0, "timestep"),
     "fp64_timestep_512": (W.CHANNEL_512, 0, 0, "timestep"),
+    "fp32_refined_timestep_256": (W.CHANNEL_256, 2, 2, "timestep"),
     "fp64_projection_256": (W.CHANNEL_256, 0, 0, "projection"),
     "fp64_projection_512": (W.CHANNEL_512, 0, 0, "projection"),
     "fp32_solve_512": (W.CHANNEL_512, 1, 0, "solve"),

@@ -160,6 +160,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   if (d->tridiag < PT_AUTO || d->tridiag > PT_PDD_EXACT) return PS_EINVAL;
   if ((long long)d->nx * d->ny * d->nz > (1LL << 34)) return PS_EUNSUPPORTED;
   if (d->ny > 8192) return PS_EUNSUPPORTED;
+  if ((long long)(d->ny + 1) * d->nz >= (1LL << 31)) return PS_EUNSUPPORTED;   // line counts are int
   for (int j = 0; j <= d->ny; ++j)
     if (!isfinite(d->y_faces[j]) || (j > 0 && !(d->y_faces[j] > d->y_faces[j - 1]))) return PS_EINVAL;
   poisson_plan_s* pl = new (std::nothrow) poisson_plan_s();
@@ -475,7 +476,9 @@ poisson_status check_finite(Exec& ex, const void* x, size_t n) {
 // large constant; the dy-weighted sum of p is accumulated by every inverse pass and each
 // correction's (0, 0) mode cancels it, so the gauge error of the FP32 transforms (invisible to
 // the residual) does not persist.
-poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
+// pair_out (PP_FP32_REFINED only): leave the result as the FP32 pair (hi, lo) in the workspace's
+// pressure buffers (the last correction accumulated into lo) instead of writing FP64 p.
+poisson_status solve_impl(Exec& ex, const void* rhs, void* p, bool pair_out = false) {
   const poisson_plan_s* pl = ex.pl;
   FwdArgs args = {};
   args.in = rhs;
@@ -506,6 +509,8 @@ poisson_status solve_impl(Exec& ex, const void* rhs, void* p) {
       PP_RET((forward_and_core<float, double>(ex, FWD_RESID, ra, GAUGE_OFFSET)));
       if (r < pl->refine) {
         PP_RET((inverse_x<float, float>(ex, r == 1 ? INV_STORE : INV_ACCUM, lo, true)));
+      } else if (pair_out) {
+        PP_RET((inverse_x<float, float>(ex, r == 1 ? INV_STORE : INV_ACCUM, lo, false)));
       } else {
         PairArgs pair{hi, r >= 2 ? lo : nullptr};   // the last pass: no pressure total needed
         PP_RET((inverse_x<float, double>(ex, INV_FINAL, (double*)p, false, pair)));
@@ -667,11 +672,13 @@ poisson_status projection_timestep(poisson_plan_t pl, void* u, void* v, void* w,
   // vb; then the FP64 correction u = u_star - dt G p written over the pairs
   PP_RET(predictor_pairs(ex, u, v, w, ub, vb, wb, dt, nu, fx));
   double* f = (double*)ub;
-  double* p = p_out ? (double*)p_out : (double*)vb;
   PP_TRY_N("divergence_df", launch_divergence_df(pl->g, ex.dt, (const float2*)u, (const float2*)v,
                                                  (const float2*)w, dt, f, ex.st));
-  PP_RET(solve_impl(ex, f, p));
-  PP_TRY_N("gradient_pairs", launch_gradient_pairs(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, ex.st));
+  PP_RET(solve_impl(ex, f, nullptr, true));   // p = hi + lo in the workspace
+  const float* hi = (const float*)(pl->ws + pl->off_pbuf);
+  const float* lo = (const float*)(pl->ws + pl->off_pbuf2);
+  PP_TRY_N("gradient_pairs", launch_gradient_pairs(pl->g, ex.dt, hi, lo, (double*)u, (double*)v, (double*)w,
+                                                   (double*)p_out, dt, ex.st));
   return PS_OK;
 }
 

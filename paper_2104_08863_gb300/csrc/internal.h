@@ -202,8 +202,10 @@ cudaError_t launch_from_pairs(double* x, size_t n, cudaStream_t st);
 cudaError_t launch_momentum_df(const Geometry& g, const DevTables& tb, const MomArgsDF& a, cudaStream_t st);
 cudaError_t launch_divergence_df(const Geometry& g, const DevTables& tb, const float2* u, const float2* v,
                                  const float2* w, double dt, double* f, cudaStream_t st);
-cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const double* p, double* u, double* v,
-                                  double* w, double dt, cudaStream_t st);
+// u = u* - dt G p with p = hi + lo (the refined solve's FP32 pair); p_out (may be null) receives
+// p in FP64.
+cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const float* hi, const float* lo, double* u,
+                                  double* v, double* w, double* p_out, double dt, cudaStream_t st);
 
 }  // namespace pp
 

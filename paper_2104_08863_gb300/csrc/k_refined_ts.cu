@@ -10,7 +10,8 @@
 //                     central differences and edge-flux sharing as k_momentum, in double-float;
 //   k_divergence_df   f = D(u*)/dt (Eq. 7) from the pairs, assembled as FP64 for the refined
 //                     Poisson solve;
-//   k_gradient_pairs  u = u* - dt G p (Eq. 4) from the pairs and the FP64 pressure, FP64 out.
+//   k_gradient_pairs  u = u* - dt G p (Eq. 4) from the pairs and the solve's FP32 pressure pair,
+//                     FP64 out.
 #include "fpconv.cuh"
 #include "internal.h"
 
@@ -139,12 +140,15 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     const df e_uv_n = top ? dmul(dadd(ldp(sv + pn + oxm), v_n), dadd(u_c, u_n)) : zero;
     const df e_vw_n = top ? dmul(dadd(ldp(sv + pn + ozm), v_n), dadd(w_c, w_n)) : zero;
     const df e_uw = dmul(dadd(w_xm, w_c), dadd(u_zm, u_c));
+    float2 bu2 = make_float2(0.f, 0.f), bw2 = bu2, bv2 = bu2;
+    if (has_base) {   // the stage-2 base values, loaded together with the stencil
+      bu2 = a.bu[pc + oc];
+      bw2 = a.bw[pc + oc];
+      if (j >= 1) bv2 = a.bv[pc + oc];
+    }
     {   // u
       df acc = fterm;
-      if (has_base) {
-        const float2 b = a.bu[pc + oc];
-        acc = dfma(alpha, df{b.x, b.y}, acc);
-      }
+      if (has_base) acc = dfma(alpha, df{bu2.x, bu2.y}, acc);
       acc = dfma(c.c0, u_c, acc);
       const df sx = dadd(u_xp, u_xm);
       acc = dfma(cDx, sx, acc);
@@ -158,10 +162,7 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     }
     {   // w
       df acc = zero;
-      if (has_base) {
-        const float2 b = a.bw[pc + oc];
-        acc = dmul(alpha, df{b.x, b.y});
-      }
+      if (has_base) acc = dmul(alpha, df{bw2.x, bw2.y});
       acc = dfma(c.c0, w_c, acc);
       const df sz = dadd(w_zp, w_zm);
       acc = dfma(cDz, sz, acc);
@@ -175,10 +176,7 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     }
     if (j >= 1) {   // v at face j
       df acc = zero;
-      if (has_base) {
-        const float2 b = a.bv[pc + oc];
-        acc = dmul(alpha, df{b.x, b.y});
-      }
+      if (has_base) acc = dmul(alpha, df{bv2.x, bv2.y});
       acc = dfma(c.v0, v_c, acc);
       const df vs = dadd(v_c, v_n);
       acc = dfma(c.vay, dmul(dsub(vs, vs_m), dadd(vs, vs_m)), acc);
@@ -211,17 +209,15 @@ __global__ void __launch_bounds__(256) k_divergence_df(Geometry g, const float2*
                                                       const double* __restrict__ inv_dy, double inv_dt,
                                                       double* __restrict__ f) {
   const size_t plane = (size_t)g.nz * g.nx;
-  const size_t total = (size_t)g.ny * plane;
-  const df cx = split(inv_dt / g.dx), cz = split(inv_dt / g.dz);
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / plane);
-    const size_t r = idx - (size_t)j * plane;
-    const int k = (int)(r / g.nx);
-    const int i = (int)(r - (size_t)k * g.nx);
+  const int nlines = g.ny * g.nz;
+  const df cx = split(inv_dt / g.dx), cz = split(inv_dt / g.dz), cdt = split(inv_dt);
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int j = line / g.nz, k = line - j * g.nz;
+    const size_t idx = (size_t)line * g.nx + i;
     const size_t oxp = idx - i + (i + 1 == g.nx ? 0 : i + 1);
     const size_t ozp = (size_t)j * plane + (size_t)(k + 1 == g.nz ? 0 : k + 1) * g.nx + i;
-    const df cy = split(inv_dt * inv_dy[j]);
+    const df cy = dmul(cdt, split(inv_dy[j]));
     df s = dmul(cx, dsub(ldp(u + oxp), ldp(u + idx)));
     s = dfma(cz, dsub(ldp(w + ozp), ldp(w + idx)), s);
     s = dfma(cy, dsub(ldp(v + idx + plane), ldp(v + idx)), s);
@@ -229,36 +225,49 @@ __global__ void __launch_bounds__(256) k_divergence_df(Geometry g, const float2*
   }
 }
 
-// u = u* - dt G p (Eq. 4): u* as pairs, p in FP64, result in FP64 (v's walls copied).
-__global__ void __launch_bounds__(256) k_gradient_pairs(Geometry g, const double* __restrict__ p, double* __restrict__ u,
+// u = u* - dt G p (Eq. 4): u* as pairs, p = hi + lo the refined solve's FP32 pair, the result in
+// FP64 (v's walls copied); the pressure differences and the products run in double-float and the
+// sums are assembled into FP64 with integer operations (no FP64 instruction per point).  p_out,
+// when given, receives p in FP64.
+__global__ void __launch_bounds__(256) k_gradient_pairs(Geometry g, const float* __restrict__ hi,
+                                                        const float* __restrict__ lo, double* __restrict__ u,
                                                         double* __restrict__ v, double* __restrict__ w,
-                                                        const double* __restrict__ inv_h, double dt) {
+                                                        double* __restrict__ p_out, const double* __restrict__ inv_h,
+                                                        double dt) {
   const size_t plane = (size_t)g.nz * g.nx;
-  const size_t total = (size_t)(g.ny + 1) * plane;
-  const double cx = dt / g.dx, cz = dt / g.dz;
+  const int nlines = (g.ny + 1) * g.nz;
+  const df cx = split(dt / g.dx), cz = split(dt / g.dz), cdt = split(dt);
   const float2* up = reinterpret_cast<const float2*>(u);
   const float2* vp = reinterpret_cast<const float2*>(v);
   const float2* wp = reinterpret_cast<const float2*>(w);
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / plane);
-    const size_t r = idx - (size_t)j * plane;
-    const int k = (int)(r / g.nx);
-    const int i = (int)(r - (size_t)k * g.nx);
+  auto P = [&](size_t o) { return df{__ldg(hi + o), __ldg(lo + o)}; };
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int j = line / g.nz, k = line - j * g.nz;
+    const size_t idx = (size_t)line * g.nx + i;
     const float2 vv = vp[idx];
-    double vn = f32_sum_to_f64(vv.x, vv.y);
+    df vn{vv.x, vv.y};
     if (j < g.ny) {
       const float2 uu = up[idx], ww = wp[idx];
-      const double pc = p[idx];
-      const double pxm = p[idx - i + (i == 0 ? g.nx - 1 : i - 1)];
-      const double pzm = p[(size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i];
-      u[idx] = f32_sum_to_f64(uu.x, uu.y) - cx * (pc - pxm);
-      w[idx] = f32_sum_to_f64(ww.x, ww.y) - cz * (pc - pzm);
-      if (j >= 1) vn -= dt * inv_h[j] * (pc - p[idx - plane]);
+      const df pc = P(idx);
+      const df pxm = P(idx - i + (i == 0 ? g.nx - 1 : i - 1));
+      const df pzm = P((size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i);
+      const df un = dsub(df{uu.x, uu.y}, dmul(cx, dsub(pc, pxm)));
+      const df wn = dsub(df{ww.x, ww.y}, dmul(cz, dsub(pc, pzm)));
+      u[idx] = f32_sum_to_f64(un.hi, un.lo);
+      w[idx] = f32_sum_to_f64(wn.hi, wn.lo);
+      if (p_out) p_out[idx] = f32_sum_to_f64(pc.hi, pc.lo);
+      if (j >= 1) {
+        const df cy = dmul(cdt, split(inv_h[j]));
+        vn = dsub(vn, dmul(cy, dsub(pc, P(idx - plane))));
+      }
     }
-    v[idx] = vn;
+    v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
   }
 }
+
+int line_grid(int nlines) { return nlines < 152 * 16 ? nlines : 152 * 16; }
+int line_block(int nx) { return nx >= 256 ? 256 : (nx + 31) / 32 * 32; }
 
 int grid_for(size_t total) {
   size_t blocks = (total + 255) / 256;
@@ -296,15 +305,14 @@ cudaError_t launch_momentum_df(const Geometry& g, const DevTables& tb, const Mom
 
 cudaError_t launch_divergence_df(const Geometry& g, const DevTables& tb, const float2* u, const float2* v,
                                  const float2* w, double dt, double* f, cudaStream_t st) {
-  const size_t total = (size_t)g.ny * g.nz * g.nx;
-  k_divergence_df<<<grid_for(total), 256, 0, st>>>(g, u, v, w, tb.d.inv_dy, 1.0 / dt, f);
+  k_divergence_df<<<line_grid(g.ny * g.nz), line_block(g.nx), 0, st>>>(g, u, v, w, tb.d.inv_dy, 1.0 / dt, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const double* p, double* u, double* v,
-                                  double* w, double dt, cudaStream_t st) {
-  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
-  k_gradient_pairs<<<grid_for(total), 256, 0, st>>>(g, p, u, v, w, tb.d.inv_h, dt);
+cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const float* hi, const float* lo, double* u,
+                                  double* v, double* w, double* p_out, double dt, cudaStream_t st) {
+  k_gradient_pairs<<<line_grid((g.ny + 1) * g.nz), line_block(g.nx), 0, st>>>(g, hi, lo, u, v, w, p_out,
+                                                                                tb.d.inv_h, dt);
   return cudaGetLastError();
 }
 

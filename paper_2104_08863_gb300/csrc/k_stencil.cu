@@ -16,14 +16,12 @@ __global__ void __launch_bounds__(256) k_gradient(Geometry g, const T* __restric
                                                   T* __restrict__ v, T* __restrict__ w,
                                                   const T* __restrict__ inv_h, T dt) {
   const size_t plane = (size_t)g.nz * g.nx;
-  const size_t total = (size_t)(g.ny + 1) * plane;
+  const int nlines = (g.ny + 1) * g.nz;
   const T cx = T(dt / g.dx), cz = T(dt / g.dz);
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / plane);
-    const size_t r = idx - (size_t)j * plane;
-    const int k = (int)(r / g.nx);
-    const int i = (int)(r - (size_t)k * g.nx);
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int j = line / g.nz, k = line - j * g.nz;
+    const size_t idx = (size_t)line * g.nx + i;
     if (j < g.ny) {
       const T pc = p[idx];
       const T pxm = p[idx - i + (i == 0 ? g.nx - 1 : i - 1)];
@@ -43,14 +41,12 @@ __global__ void __launch_bounds__(256) k_adj_epi(Geometry g, const T* __restrict
                                                  T* __restrict__ gv, T* __restrict__ gw,
                                                  const double* __restrict__ dy) {
   const size_t plane = (size_t)g.nz * g.nx;
-  const size_t total = (size_t)(g.ny + 1) * plane;
+  const int nlines = (g.ny + 1) * g.nz;
   const T ix = T(1.0 / g.dx), iz = T(1.0 / g.dz);
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / plane);
-    const size_t r = idx - (size_t)j * plane;
-    const int k = (int)(r / g.nx);
-    const int i = (int)(r - (size_t)k * g.nx);
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int j = line / g.nz, k = line - j * g.nz;
+    const size_t idx = (size_t)line * g.nx + i;
     if (j < g.ny) {
       const T dyj = T(dy[j]);
       const T pc = pp_[idx];
@@ -81,6 +77,15 @@ static int stream_grid(size_t total) {
   return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
 }
 
+// Line-wise launch of the face stencils: one CTA per x-line at a time (grid-stride over the
+// (ny+1) nz lines), threads over x, so no per-element 64-bit index division.
+static int line_grid(const Geometry& g) {
+  const int nlines = (g.ny + 1) * g.nz;
+  const int cap = 152 * 16;
+  return nlines < cap ? nlines : cap;
+}
+static int line_block(const Geometry& g) { return g.nx >= 256 ? 256 : (g.nx + 31) / 32 * 32; }
+
 template <typename T> static const T* inv_h_table(const DevTables& tb);
 template <> const double* inv_h_table<double>(const DevTables& tb) { return tb.d.inv_h; }
 template <> const float* inv_h_table<float>(const DevTables& tb) { return tb.f.inv_h; }
@@ -88,16 +93,14 @@ template <> const float* inv_h_table<float>(const DevTables& tb) { return tb.f.i
 template <typename T>
 cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
                             cudaStream_t st) {
-  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
-  k_gradient<T><<<stream_grid(total), 256, 0, st>>>(g, p, u, v, w, inv_h_table<T>(tb), T(dt));
+  k_gradient<T><<<line_grid(g), line_block(g), 0, st>>>(g, p, u, v, w, inv_h_table<T>(tb), T(dt));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, const T* q, T* gu, T* gv, T* gw,
                                     cudaStream_t st) {
-  const size_t total = (size_t)(g.ny + 1) * g.nz * g.nx;
-  k_adj_epi<T><<<stream_grid(total), 256, 0, st>>>(g, q, gu, gv, gw, tb.dy);
+  k_adj_epi<T><<<line_grid(g), line_block(g), 0, st>>>(g, q, gu, gv, gw, tb.dy);
   return cudaGetLastError();
 }
 
