@@ -80,10 +80,9 @@ __host__ __device__ __forceinline__ void f64_split(double x, float& hi, float& l
 // FP32 sum s and its exact error e (TwoSum, |e| <= ulp(s)/2) are placed into one 53-bit
 // significand, s in the top 24 bits and e (aligned and truncated) in the low 29; a borrow from an
 // opposite-signed e renormalises by one bit.  FP32 subnormals are treated as zero.
-__host__ __device__ __forceinline__ double f32_sum_to_f64(float a, float b) {
-  const float s = a + b;
-  const float bp = s - a;
-  const float e = (a - (s - bp)) + (b - bp);
+// s + e as a double for a normalised pair (|e| <= ulp(s)/2, e.g. the result of TwoSum or of a
+// double-float addition): the placement step of f32_sum_to_f64 alone.
+__host__ __device__ __forceinline__ double f32_norm_pair_to_f64(float s, float e) {
   const uint32_t us = bits_of(s), ue = bits_of(e);
   const uint32_t es = (us >> 23) & 0xffu, ee = (ue >> 23) & 0xffu;
   if (es == 0u) return 0.0;
@@ -104,6 +103,12 @@ __host__ __device__ __forceinline__ double f32_sum_to_f64(float a, float b) {
     }
   }
   return double_of(((uint64_t)(us >> 31) << 63) | ((uint64_t)ex << 52) | (R & 0xfffffffffffffull));
+}
+
+__host__ __device__ __forceinline__ double f32_sum_to_f64(float a, float b) {
+  const float s = a + b;
+  const float bp = s - a;
+  return f32_norm_pair_to_f64(s, (a - (s - bp)) + (b - bp));
 }
 
 // ---- double-float arithmetic (value = hi + lo) ----------------------------------------------

@@ -24,6 +24,33 @@ __device__ __forceinline__ df dsub(df a, df b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df dmul(df a, df b) { return df_mul(a, b); }
 __device__ __forceinline__ df dfma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 __device__ __forceinline__ df dtwice(df a) { return df{2.f * a.hi, 2.f * a.lo}; }
+// Sum of two pairs left unnormalised (TwoSum of the high parts, the low parts added): a valid
+// double-float operand for a product, three operations cheaper than dadd.
+__device__ __forceinline__ df uadd(df a, df b) {
+  const df s = two_sum_df(a.hi, b.hi);
+  return df{s.hi, s.lo + (a.lo + b.lo)};
+}
+__device__ __forceinline__ df usub(df a, df b) {
+  const df s = two_diff_df(a.hi, b.hi);
+  return df{s.hi, s.lo + (a.lo - b.lo)};
+}
+// Compensated accumulator (S, C) += c * x: the product's rounding error by FMAs, the sum's by
+// TwoSum, all error terms collected in C (the Dot2 scheme); normalised once at the end.
+struct Acc { float S, C; };
+__device__ __forceinline__ void acc_prod(Acc& a, df c, df x) {
+  const float p = c.hi * x.hi;
+  float e = fmaf(c.hi, x.hi, -p);
+  e = fmaf(c.hi, x.lo, e);
+  e = fmaf(c.lo, x.hi, e);
+  const df t = two_sum_df(a.S, p);
+  a.S = t.hi;
+  a.C += t.lo + e;
+}
+__device__ __forceinline__ Acc acc_of(df x) { return Acc{x.hi, x.lo}; }
+__device__ __forceinline__ float2 acc_out(const Acc& a) {
+  const df r = quick_two_sum_df(a.S, a.C);
+  return make_float2(r.hi, r.lo);
+}
 __device__ __forceinline__ df ldp(const float2* p) {
   const float2 v = __ldg(p);
   return df{v.x, v.y};
@@ -120,10 +147,10 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     w_m = ldp(sw + pm + oc);
     u_m_xp = ldp(su + pm + oxp);
     w_m_zp = ldp(sw + pm + ozp);
-    e_uv = dmul(dadd(ldp(sv + pc + oxm), v_c), dadd(u_m, u_c));
-    e_vw = dmul(dadd(ldp(sv + pc + ozm), v_c), dadd(w_m, w_c));
+    e_uv = dmul(uadd(ldp(sv + pc + oxm), v_c), uadd(u_m, u_c));
+    e_vw = dmul(uadd(ldp(sv + pc + ozm), v_c), uadd(w_m, w_c));
   }
-  df vs_m = dadd(v_m, v_c);
+  df vs_m = uadd(v_m, v_c);
   if (j0 == 0) a.ov[oc] = has_base ? a.bv[oc] : f2(v_c);
   for (int j = j0; j < j1; ++j) {
     const RowCoefDF c = rc[j - j0];
@@ -137,9 +164,9 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     const df w_xm = ldp(sw + pc + oxm), w_xp = ldp(sw + pc + oxp), w_zm = ldp(sw + pc + ozm), w_zp = ldp(sw + pc + ozp);
     const df w_zp_xm = ldp(sw + pc + ozp_xm);
     const df v_xm = ldp(sv + pc + oxm), v_xp = ldp(sv + pc + oxp), v_zm = ldp(sv + pc + ozm), v_zp = ldp(sv + pc + ozp);
-    const df e_uv_n = top ? dmul(dadd(ldp(sv + pn + oxm), v_n), dadd(u_c, u_n)) : zero;
-    const df e_vw_n = top ? dmul(dadd(ldp(sv + pn + ozm), v_n), dadd(w_c, w_n)) : zero;
-    const df e_uw = dmul(dadd(w_xm, w_c), dadd(u_zm, u_c));
+    const df e_uv_n = top ? dmul(uadd(ldp(sv + pn + oxm), v_n), uadd(u_c, u_n)) : zero;
+    const df e_vw_n = top ? dmul(uadd(ldp(sv + pn + ozm), v_n), uadd(w_c, w_n)) : zero;
+    const df e_uw = dmul(uadd(w_xm, w_c), uadd(u_zm, u_c));
     float2 bu2 = make_float2(0.f, 0.f), bw2 = bu2, bv2 = bu2;
     if (has_base) {   // the stage-2 base values, loaded together with the stencil
       bu2 = a.bu[pc + oc];
@@ -147,48 +174,48 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
       if (j >= 1) bv2 = a.bv[pc + oc];
     }
     {   // u
-      df acc = fterm;
-      if (has_base) acc = dfma(alpha, df{bu2.x, bu2.y}, acc);
-      acc = dfma(c.c0, u_c, acc);
-      const df sx = dadd(u_xp, u_xm);
-      acc = dfma(cDx, sx, acc);
-      acc = dfma(cAx, dmul(dsub(u_xp, u_xm), dadd(sx, dtwice(u_c))), acc);
-      acc = dfma(cDz, dadd(u_zp, u_zm), acc);
-      acc = dfma(cAz, dsub(dmul(dadd(w_zp_xm, w_zp), dadd(u_c, u_zp)), e_uw), acc);
-      acc = dfma(c.cay, dsub(e_uv_n, e_uv), acc);
-      acc = dfma(c.ca, u_m, acc);
-      acc = dfma(c.cc, u_n, acc);
-      a.ou[pc + oc] = f2(acc);
+      Acc acc = acc_of(fterm);
+      if (has_base) acc_prod(acc, alpha, df{bu2.x, bu2.y});
+      acc_prod(acc, c.c0, u_c);
+      const df sx = uadd(u_xp, u_xm);
+      acc_prod(acc, cDx, sx);
+      acc_prod(acc, cAx, dmul(usub(u_xp, u_xm), uadd(sx, dtwice(u_c))));
+      acc_prod(acc, cDz, uadd(u_zp, u_zm));
+      acc_prod(acc, cAz, usub(dmul(uadd(w_zp_xm, w_zp), uadd(u_c, u_zp)), e_uw));
+      acc_prod(acc, c.cay, usub(e_uv_n, e_uv));
+      acc_prod(acc, c.ca, u_m);
+      acc_prod(acc, c.cc, u_n);
+      a.ou[pc + oc] = acc_out(acc);
     }
     {   // w
-      df acc = zero;
-      if (has_base) acc = dmul(alpha, df{bw2.x, bw2.y});
-      acc = dfma(c.c0, w_c, acc);
-      const df sz = dadd(w_zp, w_zm);
-      acc = dfma(cDz, sz, acc);
-      acc = dfma(cAz, dmul(dsub(w_zp, w_zm), dadd(sz, dtwice(w_c))), acc);
-      acc = dfma(cDx, dadd(w_xp, w_xm), acc);
-      acc = dfma(cAx, dsub(dmul(dadd(w_c, w_xp), dadd(u_zm_xp, u_xp)), e_uw), acc);
-      acc = dfma(c.cay, dsub(e_vw_n, e_vw), acc);
-      acc = dfma(c.ca, w_m, acc);
-      acc = dfma(c.cc, w_n, acc);
-      a.ow[pc + oc] = f2(acc);
+      Acc acc{0.f, 0.f};
+      if (has_base) acc_prod(acc, alpha, df{bw2.x, bw2.y});
+      acc_prod(acc, c.c0, w_c);
+      const df sz = uadd(w_zp, w_zm);
+      acc_prod(acc, cDz, sz);
+      acc_prod(acc, cAz, dmul(usub(w_zp, w_zm), uadd(sz, dtwice(w_c))));
+      acc_prod(acc, cDx, uadd(w_xp, w_xm));
+      acc_prod(acc, cAx, usub(dmul(uadd(w_c, w_xp), uadd(u_zm_xp, u_xp)), e_uw));
+      acc_prod(acc, c.cay, usub(e_vw_n, e_vw));
+      acc_prod(acc, c.ca, w_m);
+      acc_prod(acc, c.cc, w_n);
+      a.ow[pc + oc] = acc_out(acc);
     }
     if (j >= 1) {   // v at face j
-      df acc = zero;
-      if (has_base) acc = dmul(alpha, df{bv2.x, bv2.y});
-      acc = dfma(c.v0, v_c, acc);
-      const df vs = dadd(v_c, v_n);
-      acc = dfma(c.vay, dmul(dsub(vs, vs_m), dadd(vs, vs_m)), acc);
-      acc = dfma(cDx, dadd(v_xp, v_xm), acc);
-      acc = dfma(cAx, dsub(dmul(dadd(v_c, v_xp), dadd(u_m_xp, u_xp)), e_uv), acc);
-      acc = dfma(cDz, dadd(v_zp, v_zm), acc);
-      acc = dfma(cAz, dsub(dmul(dadd(v_c, v_zp), dadd(w_m_zp, w_zp)), e_vw), acc);
-      acc = dfma(c.va, v_m, acc);
-      acc = dfma(c.vc, v_n, acc);
-      a.ov[pc + oc] = f2(acc);
+      Acc acc{0.f, 0.f};
+      if (has_base) acc_prod(acc, alpha, df{bv2.x, bv2.y});
+      acc_prod(acc, c.v0, v_c);
+      const df vs = uadd(v_c, v_n);
+      acc_prod(acc, c.vay, dmul(usub(vs, vs_m), uadd(vs, vs_m)));
+      acc_prod(acc, cDx, uadd(v_xp, v_xm));
+      acc_prod(acc, cAx, usub(dmul(uadd(v_c, v_xp), uadd(u_m_xp, u_xp)), e_uv));
+      acc_prod(acc, cDz, uadd(v_zp, v_zm));
+      acc_prod(acc, cAz, usub(dmul(uadd(v_c, v_zp), uadd(w_m_zp, w_zp)), e_vw));
+      acc_prod(acc, c.va, v_m);
+      acc_prod(acc, c.vc, v_n);
+      a.ov[pc + oc] = acc_out(acc);
     }
-    vs_m = dadd(v_c, v_n);
+    vs_m = uadd(v_c, v_n);
     u_m = u_c; u_c = u_n;
     w_m = w_c; w_c = w_n;
     v_m = v_c; v_c = v_n;
@@ -211,17 +238,18 @@ __global__ void __launch_bounds__(256) k_divergence_df(Geometry g, const float2*
   const size_t plane = (size_t)g.nz * g.nx;
   const int nlines = g.ny * g.nz;
   const df cx = split(inv_dt / g.dx), cz = split(inv_dt / g.dz), cdt = split(inv_dt);
-  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
-  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
     const int j = line / g.nz, k = line - j * g.nz;
-    const size_t idx = (size_t)line * g.nx + i;
-    const size_t oxp = idx - i + (i + 1 == g.nx ? 0 : i + 1);
-    const size_t ozp = (size_t)j * plane + (size_t)(k + 1 == g.nz ? 0 : k + 1) * g.nx + i;
     const df cy = dmul(cdt, split(inv_dy[j]));
-    df s = dmul(cx, dsub(ldp(u + oxp), ldp(u + idx)));
-    s = dfma(cz, dsub(ldp(w + ozp), ldp(w + idx)), s);
-    s = dfma(cy, dsub(ldp(v + idx + plane), ldp(v + idx)), s);
-    f[idx] = f32_sum_to_f64(s.hi, s.lo);
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t idx = (size_t)line * g.nx + i;
+      const size_t oxp = idx - i + (i + 1 == g.nx ? 0 : i + 1);
+      const size_t ozp = (size_t)j * plane + (size_t)(k + 1 == g.nz ? 0 : k + 1) * g.nx + i;
+      df s = dmul(cx, dsub(ldp(u + oxp), ldp(u + idx)));
+      s = dfma(cz, dsub(ldp(w + ozp), ldp(w + idx)), s);
+      s = dfma(cy, dsub(ldp(v + idx + plane), ldp(v + idx)), s);
+      f[idx] = f32_norm_pair_to_f64(s.hi, s.lo);
+    }
   }
 }
 
@@ -241,28 +269,33 @@ __global__ void __launch_bounds__(256) k_gradient_pairs(Geometry g, const float*
   const float2* vp = reinterpret_cast<const float2*>(v);
   const float2* wp = reinterpret_cast<const float2*>(w);
   auto P = [&](size_t o) { return df{__ldg(hi + o), __ldg(lo + o)}; };
-  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
-  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
     const int j = line / g.nz, k = line - j * g.nz;
-    const size_t idx = (size_t)line * g.nx + i;
-    const float2 vv = vp[idx];
-    df vn{vv.x, vv.y};
-    if (j < g.ny) {
-      const float2 uu = up[idx], ww = wp[idx];
-      const df pc = P(idx);
-      const df pxm = P(idx - i + (i == 0 ? g.nx - 1 : i - 1));
-      const df pzm = P((size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i);
-      const df un = dsub(df{uu.x, uu.y}, dmul(cx, dsub(pc, pxm)));
-      const df wn = dsub(df{ww.x, ww.y}, dmul(cz, dsub(pc, pzm)));
-      u[idx] = f32_sum_to_f64(un.hi, un.lo);
-      w[idx] = f32_sum_to_f64(wn.hi, wn.lo);
-      if (p_out) p_out[idx] = f32_sum_to_f64(pc.hi, pc.lo);
-      if (j >= 1) {
-        const df cy = dmul(cdt, split(inv_h[j]));
-        vn = dsub(vn, dmul(cy, dsub(pc, P(idx - plane))));
+    const df cy = (j >= 1 && j < g.ny) ? dmul(cdt, split(inv_h[j])) : df{0.f, 0.f};
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t idx = (size_t)line * g.nx + i;
+      const float2 vv = vp[idx];
+      df vn{vv.x, vv.y};
+      if (j < g.ny) {
+        const float2 uu = up[idx], ww = wp[idx];
+        const df pc = P(idx);
+        const df pxm = P(idx - i + (i == 0 ? g.nx - 1 : i - 1));
+        const df pzm = P((size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i);
+        const df un = dsub(df{uu.x, uu.y}, dmul(cx, dsub(pc, pxm)));
+        const df wn = dsub(df{ww.x, ww.y}, dmul(cz, dsub(pc, pzm)));
+        u[idx] = f32_norm_pair_to_f64(un.hi, un.lo);
+        w[idx] = f32_norm_pair_to_f64(wn.hi, wn.lo);
+        if (p_out) p_out[idx] = f32_sum_to_f64(pc.hi, pc.lo);
+        if (j >= 1) {
+          vn = dsub(vn, dmul(cy, dsub(pc, P(idx - plane))));
+          v[idx] = f32_norm_pair_to_f64(vn.hi, vn.lo);
+        } else {
+          v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
+        }
+      } else {
+        v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
       }
     }
-    v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
   }
 }
 
