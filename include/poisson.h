@@ -57,7 +57,11 @@ typedef enum {
 typedef enum {
   PT_AUTO = 0,            /* PDD (exact reduced system) with an automatic partition      */
   PT_THOMAS = 1,          /* one serial Thomas sweep per system (pdd_parts = 1)          */
-  PT_PDD_EXACT = 2        /* PDD with pdd_parts sub-blocks, exact reduced system Eq. 21  */
+  PT_PDD_EXACT = 2,       /* PDD with pdd_parts sub-blocks, exact reduced system Eq. 21  */
+  PT_PDD_TRUNCATED = 3    /* PDD as in Sec. 2.2: the framed coupling entries of Eq. 21   */
+                          /* dropped, each interface an independent 2x2 system (exact    */
+                          /* only when the spikes have decayed across a block; the modes */
+                          /* that PP_FP32* solve in FP64 stay exact)                     */
 } poisson_tridiag;
 
 #define POISSON_CHECK_FINITE 0x1u   /* flag: scan inputs, set PS_ENONFINITE on NaN/Inf     */

@@ -40,11 +40,11 @@ the staggered differences, conservation, self-adjoint diffusion, Heun vs its Tay
 from .grid import Grid
 from .stencils import divergence, gradient, laplacian, divergence_T, gradient_T
 from .tridiag import thomas, pdd
-from .poisson import solve, solve_transposed, project, project_adjoint, residual
+from .poisson import solve, solve_pdd, solve_transposed, project, project_adjoint, residual
 from .momentum import momentum_rhs, rk2_predictor, timestep
 
 __all__ = [
     "Grid", "divergence", "gradient", "laplacian", "divergence_T", "gradient_T",
-    "thomas", "pdd", "solve", "solve_transposed", "project", "project_adjoint", "residual",
+    "thomas", "pdd", "solve", "solve_pdd", "solve_transposed", "project", "project_adjoint", "residual",
     "momentum_rhs", "rk2_predictor", "timestep",
 ]

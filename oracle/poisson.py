@@ -16,7 +16,7 @@ import numpy as np
 
 from .grid import Grid
 from .stencils import divergence, gradient, laplacian, divergence_T, gradient_T
-from .tridiag import thomas
+from .tridiag import thomas, pdd
 
 _CHUNK = 64          # kz planes per Thomas call (memory only; the systems are independent)
 
@@ -84,6 +84,30 @@ def solve(g: Grid, f):
     fc = f - _weighted_mean(g, f)
     F = np.fft.fft2(fc, axes=(1, 2))
     P = _spectral_solve(g, F, transposed=False)
+    return np.fft.ifft2(P, axes=(1, 2)).real
+
+
+def solve_pdd(g: Grid, f, parts: int, truncated: bool, exact_modes=None):
+    """``solve`` with every wall-normal system of Eq. 9 solved by the PDD algorithm of Sec. 2.2
+    (``tridiag.pdd``): with the exact reduced system, or truncated as in the paper (the framed
+    coupling entries dropped).  ``exact_modes(kx, kz)`` (signed kx, kz) may name modes that keep
+    the exact reduced system.  One mode at a time: for small grids only."""
+    f = np.asarray(f, dtype=np.float64)
+    fc = f - _weighted_mean(g, f)
+    F = np.fft.fft2(fc, axes=(1, 2))
+    a, c = g.lower, g.upper
+    lamx, lamz = g.lambda_x(), g.lambda_z()
+    P = np.empty_like(F)
+    for kz in range(g.nz):
+        for kx in range(g.nx):
+            if kx == 0 and kz == 0:
+                continue
+            skx = kx if kx <= g.nx // 2 else kx - g.nx
+            skz = kz if kz <= g.nz // 2 else kz - g.nz
+            trunc = truncated and not (exact_modes is not None and exact_modes(skx, skz))
+            diag = -(a + c) + lamx[kx] + lamz[kz]
+            P[:, kz, kx] = pdd(a, diag, c, F[:, kz, kx], parts, truncated=trunc)
+    P[:, 0, 0] = _bordered_mode00(g, F[:, 0, 0], transposed=False)
     return np.fft.ifft2(P, axes=(1, 2)).real
 
 

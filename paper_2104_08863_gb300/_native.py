@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libpoisson.so")
 
 PS_OK, PS_EINVAL, PS_EUNSUPPORTED, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ENOWORKSPACE = range(8)
 PP_FP64, PP_FP32, PP_FP32_REFINED = 0, 1, 2
-PT_AUTO, PT_THOMAS, PT_PDD_EXACT = 0, 1, 2
+PT_AUTO, PT_THOMAS, PT_PDD_EXACT, PT_PDD_TRUNCATED = 0, 1, 2, 3
 POISSON_STATIC_WS_MAX_BYTES = 8 * 1024 * 1024
 POISSON_CHECK_FINITE = 0x1
 POISSON_TIMING = 0x2

@@ -157,7 +157,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   if (d->nx < 4 || d->ny < 2 || d->nz < 2 || (d->nx & 1)) return PS_EINVAL;
   if (!(d->lx > 0.0) || !(d->lz > 0.0) || !d->y_faces) return PS_EINVAL;
   if (d->precision < PP_FP64 || d->precision > PP_FP32_REFINED) return PS_EINVAL;
-  if (d->tridiag < PT_AUTO || d->tridiag > PT_PDD_EXACT) return PS_EINVAL;
+  if (d->tridiag < PT_AUTO || d->tridiag > PT_PDD_TRUNCATED) return PS_EINVAL;
   if ((long long)d->nx * d->ny * d->nz > (1LL << 34)) return PS_EUNSUPPORTED;
   if (d->ny > 8192) return PS_EUNSUPPORTED;
   if ((long long)(d->ny + 1) * d->nz >= (1LL << 31)) return PS_EUNSUPPORTED;   // line counts are int
@@ -336,7 +336,8 @@ poisson_status poisson_set_workspace(poisson_plan_t pl, void* ws, size_t bytes, 
   pl->ws = base;
   pl->dt = pp::bind_tables(pl, base);
   if (!pl->has_tri && pl->parts > 1) {
-    if (launch_reduced_setup(pl->g, pl->dt, pl->parts, (float*)(base + pl->off_red), st) != cudaSuccess)
+    if (launch_reduced_setup(pl->g, pl->dt, pl->parts, pl->tridiag == PT_PDD_TRUNCATED, (float*)(base + pl->off_red),
+                             st) != cudaSuccess)
       return PS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
   }
@@ -405,7 +406,7 @@ poisson_status spectral_core<double>(Exec& ex, cplx<double>* spec, GaugeMode gau
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
   PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, ex.dt, pl->fz, -1, spec, st));
-  PP_TRY_N("tridiag_pdd", launch_tridiag_factored(g, ex.dt, pl->parts, spec, st));
+  PP_TRY_N("tridiag_pdd", launch_tridiag_factored(g, ex.dt, pl->parts, pl->tridiag == PT_PDD_TRUNCATED, spec, st));
   PP_TRY_N("mode00", launch_mode00<double>(g, ex.dt, gauge, spec, st));
   PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, ex.dt, pl->fz, +1, spec, st));
   return PS_OK;
@@ -417,7 +418,9 @@ poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
   PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
-  if (pl->has_tri) PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, spec, st));
+  if (pl->has_tri)
+    PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, pl->tridiag == PT_PDD_TRUNCATED,
+                                                        spec, st));
   else PP_TRY_N("tridiag_pdd", launch_tridiag_reg_f32(g, ex.dt, pl->parts, pl->low, spec, st));
   if (pl->low >= 0) {
     cplx<double>* scr = (cplx<double>*)(ex.ws + pl->off_scratch);

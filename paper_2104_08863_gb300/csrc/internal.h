@@ -134,9 +134,10 @@ cudaError_t launch_tridiag<float, float>(const Geometry& g, const DevTables& tb,
 
 // PDD with the precomputed factors tb.tri_d / tb.tri_f (setup once per plan, then per solve).
 cudaError_t launch_tridiag_setup(const Geometry& g, const DevTables& tb, int parts, cudaStream_t st);
-cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, cplx<double>* spec,
+// trunc: the truncated reduced system of Sec. 2.2 (framed coupling entries dropped).
+cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, bool trunc, cplx<double>* spec,
                                     cudaStream_t st);
-cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes, bool trunc,
                                         cplx<float>* spec, cudaStream_t st);
 
 // FP32 PDD with each block of m = ny/P rows held in one thread's registers and its factors
@@ -152,7 +153,8 @@ cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int p
                                    cplx<float>* spec, cudaStream_t st);
 // Bytes of the reduced-system table of the register kernel, and its FP64 set-up (once per plan).
 size_t reduced_table_bytes(const Geometry& g, int parts);
-cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, float* tab, cudaStream_t st);
+cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, bool trunc, float* tab,
+                                 cudaStream_t st);
 
 // FP64 re-solve of the low-mode list on FP32 spectral data (intermediates in FP64 scratch).
 cudaError_t launch_tridiag_low64(const Geometry& g, const DevTables& tb, int parts, int low_modes,

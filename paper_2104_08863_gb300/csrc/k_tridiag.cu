@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_tridiag_setup(Geometry g, int P, int m,
 }
 
 template <typename T, bool FULL>
-__global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int m, int S, int low,
+__global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int m, int S, int low, int trunc,
                                                           const T* __restrict__ a, const T* __restrict__ c,
                                                           TriFactors<T> tf, cplx<T>* __restrict__ spec) {
   constexpr int CH = 8;
@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int
       for (int i = 0; i < P - 1; ++i) {
         const int ii = i * S + s, in = (i + 1) * S + s;
         const size_t bi = (size_t)i * nsys + sys, bn = (size_t)(i + 1) * nsys + sys;
-        const T vLi = tf.vL[bi], wLi = tf.wL[bi], vFn = tf.vF[bn], wFi = tf.wF[bi];
+        // truncated (Sec. 2.2): the framed entries v_m^i and w_1^{i+1} of Z are dropped
+        const T vLi = trunc ? T(0) : tf.vL[bi], wLi = tf.wL[bi], vFn = tf.vF[bn], wFi = tf.wF[bi];
         // eliminating z_{i-1} fills entry (0,1): L_i reaches F_{i+1} through L_{i-1} and F_i
         const T d01 = -wLi - vLi * wFi * pX01, d10 = -vFn;
         const T inv = T(1) / (T(1) - d01 * d10);
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(256) k_tridiag_factored(Geometry g, int P, int
       cplx<T> z1n = mk<T>(T(0), T(0));
       for (int i = P - 2; i >= 0; --i) {
         const int ii = i * S + s;
-        const T tw = (i == P - 2) ? T(0) : tf.wF[(size_t)(i + 1) * nsys + sys];
+        const T tw = (i == P - 2 || trunc) ? T(0) : tf.wF[(size_t)(i + 1) * nsys + sys];
         const cplx<T> z0 = mk<T>(y0r[ii] + tw * z1n.x * X01s[ii], y0i[ii] + tw * z1n.y * X01s[ii]);
         const cplx<T> z1 = mk<T>(y1r[ii] + tw * z1n.x * X11s[ii], y1i[ii] + tw * z1n.y * X11s[ii]);
         alr[(i + 1) * S + s] = z0.x; ali[(i + 1) * S + s] = z0.y;   // alpha of block i+1 = L_i
@@ -467,7 +468,7 @@ __device__ void block_spikes64(const double* a, const double* c, double sigma, i
   wL = c[r0 + m - 1] * rbp;
 }
 
-__global__ void __launch_bounds__(128) k_reduced_setup(Geometry g, int P, int m, const double* __restrict__ a,
+__global__ void __launch_bounds__(128) k_reduced_setup(Geometry g, int P, int m, int trunc, const double* __restrict__ a,
                                                       const double* __restrict__ c, const double* __restrict__ lamx,
                                                       const double* __restrict__ lamz, float* __restrict__ tab) {
   const int nsys = g.nz * g.ncols;
@@ -482,15 +483,17 @@ __global__ void __launch_bounds__(128) k_reduced_setup(Geometry g, int P, int m,
   for (int i = 0; i < P - 1; ++i) {
     double vF1, vL1, wF1, wL1;
     block_spikes64(a, c, sigma, (i + 1) * m, m, vF1, vL1, wF1, wL1);
-    const double d01 = -wL0 - vL0 * wF0 * pX01, d10 = -vF1;
+    // truncated (Sec. 2.2): without the framed entries v_m^i, w_1^{i+1} every interface is an
+    // independent 2x2 system (no recurrence: vL and tw stored as 0)
+    const double d01 = trunc ? -wL0 : -wL0 - vL0 * wF0 * pX01, d10 = -vF1;
     const double inv = 1.0 / (1.0 - d01 * d10);
     const double X01 = -d01 * inv, X10 = -d10 * inv;
     float* t = tab + ((size_t)sys * (P - 1) + i) * 5;
-    t[0] = float(vL0);
+    t[0] = trunc ? 0.f : float(vL0);
     t[1] = float(inv);
     t[2] = float(X01);
     t[3] = float(X10);
-    t[4] = i + 1 < P - 1 ? float(wF1) : 0.f;
+    t[4] = (i + 1 < P - 1 && !trunc) ? float(wF1) : 0.f;
     pX01 = X01;
     vF0 = vF1; vL0 = vL1; wF0 = wF1; wL0 = wL1;
   }
@@ -943,7 +946,7 @@ cudaError_t launch_tridiag_setup(const Geometry& g, const DevTables& tb, int par
 
 template <typename T, bool FULL>
 static cudaError_t launch_factored(const Geometry& g, const T* a, const T* c, const TriFactors<T>& tf, int parts,
-                                   int low, cplx<T>* spec, cudaStream_t st) {
+                                   int low, bool trunc, cplx<T>* spec, cudaStream_t st) {
   int S = 256 / parts;
   if (S < 1) S = 1;
   if (S > 32) S = 32;
@@ -952,7 +955,7 @@ static cudaError_t launch_factored(const Geometry& g, const T* a, const T* c, co
   auto kern = k_tridiag_factored<T, FULL>;
   cudaError_t e;
   if ((e = prep(kern, smem)) != cudaSuccess) return e;
-  kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, low, a, c, tf, spec);
+  kern<<<blocks, parts * S, smem, st>>>(g, parts, g.ny / parts, S, low, trunc ? 1 : 0, a, c, tf, spec);
   return cudaGetLastError();
 }
 
@@ -960,10 +963,12 @@ size_t reduced_table_bytes(const Geometry& g, int parts) {
   return parts > 1 ? (size_t)5 * (parts - 1) * g.nz * g.ncols * sizeof(float) : 0;
 }
 
-cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, float* tab, cudaStream_t st) {
+cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, bool trunc, float* tab,
+                                 cudaStream_t st) {
   if (parts <= 1) return cudaSuccess;
   const int nsys = g.nz * g.ncols;
-  k_reduced_setup<<<(nsys + 127) / 128, 128, 0, st>>>(g, parts, g.ny / parts, tb.d.a, tb.d.c, tb.lamx, tb.lamz, tab);
+  k_reduced_setup<<<(nsys + 127) / 128, 128, 0, st>>>(g, parts, g.ny / parts, trunc ? 1 : 0, tb.d.a, tb.d.c, tb.lamx,
+                                                       tb.lamz, tab);
   return cudaGetLastError();
 }
 
@@ -1013,14 +1018,14 @@ cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int p
   return cudaGetLastError();
 }
 
-cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, cplx<double>* spec,
+cudaError_t launch_tridiag_factored(const Geometry& g, const DevTables& tb, int parts, bool trunc, cplx<double>* spec,
                                     cudaStream_t st) {
-  return launch_factored<double, true>(g, tb.d.a, tb.d.c, tb.tri_d, parts, -1, spec, st);
+  return launch_factored<double, true>(g, tb.d.a, tb.d.c, tb.tri_d, parts, -1, trunc, spec, st);
 }
 
-cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
+cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes, bool trunc,
                                         cplx<float>* spec, cudaStream_t st) {
-  return launch_factored<float, false>(g, tb.f.a, tb.f.c, tb.tri_f, parts, low_modes, spec, st);
+  return launch_factored<float, false>(g, tb.f.a, tb.f.c, tb.tri_f, parts, low_modes, trunc, spec, st);
 }
 
 template <typename TD>

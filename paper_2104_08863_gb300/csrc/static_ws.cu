@@ -54,7 +54,8 @@ extern "C" poisson_status poisson_solve_static_ws(poisson_plan_t pl, const void*
   if (cudaMemsetAsync(ws + pl->off_status, 0, 256, st) != cudaSuccess) return PS_ECUDA;
   const pp::DevTables dt = pp::bind_tables(pl, ws);
   if (pl->has_tri && pp::launch_tridiag_setup(pl->g, dt, pl->parts, st) != cudaSuccess) return PS_ECUDA;
-  if (!pl->has_tri && pp::launch_reduced_setup(pl->g, dt, pl->parts, (float*)(ws + pl->off_red), st) != cudaSuccess)
+  if (!pl->has_tri && pp::launch_reduced_setup(pl->g, dt, pl->parts, pl->tridiag == PT_PDD_TRUNCATED,
+                                               (float*)(ws + pl->off_red), st) != cudaSuccess)
     return PS_ECUDA;
   return pp::solve_on_workspace(pl, ws, dt, rhs, p, st);
 }

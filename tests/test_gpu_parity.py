@@ -231,3 +231,36 @@ def test_bad_arguments_are_rejected(P):
     assert L.poisson_solve(plan._h, 0, buf.data_ptr(), 0) == _native.PS_EINVAL
     assert L.projection_step(plan._h, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 0, -1.0, 0) == \
         _native.PS_EINVAL
+
+
+# ------------------------------------------------------------------ truncated PDD (Sec. 2.2)
+
+@pytest.mark.parametrize("parts", [3, 4, 8])
+def test_fp64_truncated_pdd_matches_oracle_truncated(P, parts):
+    """PT_PDD_TRUNCATED drops the framed coupling entries of Z as the paper does; on the stretched
+    channel that changes the weak modes by O(1e-2), and the GPU must reproduce exactly that."""
+    nx, ny, nz = 32, 48, 16
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(10, nx, ny, nz))
+    want = oracle.solve_pdd(g, f, parts, truncated=True)
+    exact = oracle.solve(g, f)
+    assert relerr(want, exact) > 1e-4          # the truncation is visible on this grid
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, tridiag=P.PT_PDD_TRUNCATED, pdd_parts=parts, device=DEV)
+    got = solve_gpu(P, plan, f)
+    assert relerr(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("parts", [3, 4, 8])
+def test_fp32_truncated_pdd_matches_oracle_truncated(P, parts):
+    """FP32 truncated PDD (the reduced-system table built without the coupling); the lowest modes
+    that the FP32 form solves in FP64 keep the exact reduced system."""
+    nx, ny, nz, L = 32, 48, 16, 4
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(11, nx, ny, nz))
+    want = oracle.solve_pdd(g, f, parts, truncated=True, exact_modes=lambda kx, kz: abs(kx) <= L and abs(kz) <= L)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32, tridiag=P.PT_PDD_TRUNCATED, pdd_parts=parts,
+                  fp64_low_modes=L, device=DEV)
+    got = solve_gpu(P, plan, f, dtype=torch.float32)
+    assert relerr(got, want) <= 2e-5

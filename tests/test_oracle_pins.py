@@ -326,3 +326,38 @@ def test_projection_adjoint_brute_force_and_dot_product():
     lhs = sum(np.sum(a * b) for a, b in zip(Pd, wgt))
     rhs = sum(np.sum(a * b) for a, b in zip(d, PTw))
     assert abs(lhs - rhs) <= 1e-12 * sum(np.sum(np.abs(a * b)) for a, b in zip(d, PTw))
+
+
+# ---------------------------------------------------------------- PDD inside the Poisson solve
+
+@pytest.mark.parametrize("parts", [2, 4, 8])
+def test_solve_pdd_exact_equals_the_thomas_solve(parts):
+    g = _grid(16, 32, 12, stretch=2.0)
+    f = oracle.divergence(g, *W.random_velocity(7, g.nx, g.ny, g.nz))
+    want = oracle.solve(g, f)
+    got = oracle.solve_pdd(g, f, parts, truncated=False)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_solve_pdd_truncated_two_blocks_has_nothing_to_drop():
+    # with two blocks Z is a single 2x2 system: no framed entry exists (Eq. 21)
+    g = _grid(16, 32, 12, stretch=2.0)
+    f = oracle.divergence(g, *W.random_velocity(8, g.nx, g.ny, g.nz))
+    want = oracle.solve(g, f)
+    got = oracle.solve_pdd(g, f, 2, truncated=True)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_solve_pdd_truncation_error_decays_with_the_weakest_wavenumber():
+    # Sec. 2.2: the dropped entries are the far ends of the spikes, which decay across a block like
+    # exp(-sqrt(sigma) L_block); sigma >= (2 pi / L)^2 for the weakest non-(0,0) mode, so with the
+    # block length fixed (uniform y, P = 4) shrinking the periodic lengths L drives the truncation
+    # error from O(1) to rounding, and the channel's own weak modes keep it large.
+    errs = []
+    for L in (2 * np.pi, np.pi / 4, np.pi / 32):
+        g = oracle.Grid(16, 12, W.uniform_faces(64), lx=L, lz=L)
+        f = oracle.divergence(g, *W.random_velocity(9, g.nx, g.ny, g.nz))
+        want = oracle.solve(g, f)
+        got = oracle.solve_pdd(g, f, 4, truncated=True)
+        errs.append(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    assert errs[0] > 0.05 and 1e-4 < errs[1] < 1e-2 and errs[2] < 1e-13
