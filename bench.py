@@ -526,6 +526,63 @@ def batch_form(dev, steps: int = 5, warmup: int = 2, tune: bool = True):
     return out
 
 
+def pdd_study(dev):
+    """Truncated PDD (Sec. 2.2: framed entries of Z dropped) against the exact reduced system.
+
+    Part 1 (CPU, oracle, one wall-normal system): the truncation error of a single mode as a
+    function of sigma = -(lambda_x + lambda_z) on the 384-row (tanh 2.0) and 768-row (tanh 2.2)
+    grids for several P, against the Thomas solution; the paper's condition is that the dropped
+    spike ends fall below machine accuracy.  Part 2 (GPU): whole solves on the 512x384x512 (FP64)
+    and 1536x768x1024 (FP32) channels, max |p_trunc - p_exact| / max |p_exact| and times.
+    """
+    import oracle
+    import torch
+    import paper_2104_08863_gb300 as P
+    out = {"per_sigma": {}, "solves": {}}
+    rng = np.random.default_rng(12)
+    for ny, s in ((384, 2.0), (768, 2.2)):
+        g = oracle.Grid(8, 8, W.tanh_faces(ny, s))
+        a, c = g.lower, g.upper
+        d = rng.standard_normal(ny) + 1j * rng.standard_normal(ny)
+        rows = {}
+        for parts in (4, 8, 16, 32):
+            errs = {}
+            for sigma in (1e0, 1e1, 1e2, 1e3, 1e4, 1e5):
+                diag = -(a + c) - sigma
+                x = oracle.thomas(a, diag, c, d)
+                xt = oracle.pdd(a, diag, c, d, parts, truncated=True)
+                errs[f"{sigma:.0e}"] = float(np.max(np.abs(xt - x)) / np.max(np.abs(x)))
+            rows[f"P={parts} (m={ny // parts})"] = errs
+        out["per_sigma"][f"ny={ny} tanh {s}"] = rows
+    gen = torch.Generator(device=dev)
+    for case, prec, parts_list in ((CASE, P.PP_FP64, (4, 8, 16)), (W.CHANNEL_1536, P.PP_FP32, (8, 16, 32))):
+        faces = W.tanh_faces(case.ny, case.stretch)
+        gen.manual_seed(2)
+        dtype = torch.float64 if prec == P.PP_FP64 else torch.float32
+        f = torch.randn(case.ny, case.nz, case.nx, dtype=dtype, device=dev, generator=gen)
+        res = {}
+        for parts in parts_list:
+            sol = {}
+            for tri in (P.PT_PDD_EXACT, P.PT_PDD_TRUNCATED):
+                plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, tridiag=tri,
+                              pdd_parts=parts, flags=P.POISSON_TIMING, device=dev)
+                p = torch.empty_like(f)
+                plan.solve(f, out=p)
+                plan.solve(f, out=p)
+                tri_ms = sum(ms for k, ms in plan.stage_times() if k.startswith("tridiag"))
+                sol[tri] = (p, tri_ms)
+                del plan
+            pe, pt = sol[P.PT_PDD_EXACT][0], sol[P.PT_PDD_TRUNCATED][0]
+            res[f"P={parts}"] = {"maxrel_trunc_vs_exact": float((pt - pe).abs().max() / pe.abs().max()),
+                                 "tridiag_ms_exact": sol[P.PT_PDD_EXACT][1],
+                                 "tridiag_ms_truncated": sol[P.PT_PDD_TRUNCATED][1]}
+            del sol, pe, pt
+            torch.cuda.empty_cache()
+        out["solves"][f"{case.name} {'FP64' if prec == P.PP_FP64 else 'FP32'}"] = res
+        del f
+    return out
+
+
 PROFILE_CASES = {
     # name: (case, precision, refine_steps, kind) with kind "timestep", "projection" or "solve"
     "fp64_timestep_256": (W.CHANNEL_256, 0, 0, "timestep"),
@@ -590,6 +647,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the 1536x768x1024 precision-form comparison")
     ap.add_argument("--forms-only", action="store_true")
     ap.add_argument("--batch-only", action="store_true", help="only the 64-instance batched form")
+    ap.add_argument("--pdd-study", action="store_true", help="truncated vs exact PDD (Sec. 2.2) study")
     ap.add_argument("--profile", choices=sorted(PROFILE_CASES), help="run a named case for ncu, no timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -598,6 +656,11 @@ def main():
         profile_case(args.profile)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.pdd_study:
+        import torch
+        from paper_2104_08863_gb300 import build as b
+        b.build()
+        print(json.dumps(pdd_study(torch.device("cuda", 0))))
     elif args.batch_only:
         import torch
         from paper_2104_08863_gb300 import build as b
