@@ -598,6 +598,9 @@ PROFILE_CASES = {
     # the 1536-point x lines of the 1536x768x1024 precision form on a 96x128 (y, z) section
     "fp32_refined_solve_1536x96x128": (W.ChannelCase("channel_1536x96x128_tanh2.2", 1536, 96, 128, 2.2), 2, 1,
                                        "solve"),
+    # the full 1536 x 1024 planes of the precision form at 64 rows (a fifth entry would add plan flags)
+    "fp32_refined_solve_1536x64x1024": (W.ChannelCase("channel_1536x64x1024_tanh2.2", 1536, 64, 1024, 2.2), 2, 1,
+                                        "solve"),
 }
 
 
@@ -607,12 +610,13 @@ def profile_case(name: str, repeats: int = 2):
     from paper_2104_08863_gb300 import build as b
     b.build()
     import paper_2104_08863_gb300 as P
-    case, prec, steps, kind = PROFILE_CASES[name]
+    case, prec, steps, kind = PROFILE_CASES[name][:4]
+    extra = PROFILE_CASES[name][4] if len(PROFILE_CASES[name]) > 4 else 0
     dev = torch.device("cuda", 0)
     faces = W.tanh_faces(case.ny, case.stretch)
     parts = PDD_PARTS if (prec == P.PP_FP64 and case.ny % PDD_PARTS == 0) else 0
     plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=parts,
-                  refine_steps=max(steps, 1), device=dev)
+                  refine_steps=max(steps, 1), flags=extra, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     dtype = torch.float32 if prec == P.PP_FP32 else torch.float64

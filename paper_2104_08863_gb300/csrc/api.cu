@@ -395,29 +395,26 @@ void timer_end(Exec& ex, const char* name) {
     if (_s != PS_OK) return _s;          \
   } while (0)
 
-// Spectral middle of a solve on the spectral buffer: forward z-FFT, wall-normal systems,
-// (0, 0) mode, inverse z-FFT.
+// Spectral middle of a solve on the z-transformed spectral buffer: wall-normal systems and the
+// (0, 0) mode.
 template <typename T>
-poisson_status spectral_core(Exec& ex, cplx<T>* spec, GaugeMode gauge);
+poisson_status spectral_mid(Exec& ex, cplx<T>* spec, GaugeMode gauge);
 
 template <>
-poisson_status spectral_core<double>(Exec& ex, cplx<double>* spec, GaugeMode gauge) {
+poisson_status spectral_mid<double>(Exec& ex, cplx<double>* spec, GaugeMode gauge) {
   const poisson_plan_s* pl = ex.pl;
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
-  PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, ex.dt, pl->fz, -1, spec, st));
   PP_TRY_N("tridiag_pdd", launch_tridiag_factored(g, ex.dt, pl->parts, pl->tridiag == PT_PDD_TRUNCATED, spec, st));
   PP_TRY_N("mode00", launch_mode00<double>(g, ex.dt, gauge, spec, st));
-  PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, ex.dt, pl->fz, +1, spec, st));
   return PS_OK;
 }
 
 template <>
-poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge) {
+poisson_status spectral_mid<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge) {
   const poisson_plan_s* pl = ex.pl;
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
-  PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
   if (pl->has_tri)
     PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, pl->tridiag == PT_PDD_TRUNCATED,
                                                         spec, st));
@@ -427,25 +424,28 @@ poisson_status spectral_core<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge
     PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, st));
   }
   PP_TRY_N("mode00", launch_mode00<float>(g, ex.dt, gauge, spec, st));
-  PP_TRY_N("fft_z_inv", launch_fft_z<float>(g, ex.dt, pl->fz, +1, spec, st));
   return PS_OK;
 }
 
+// Forward x- and z-transforms of the right-hand side of `mode`, then the spectral middle.
 template <typename T, typename TI>
 poisson_status forward_and_core(Exec& ex, FwdMode mode, const FwdArgs& args, GaugeMode gauge) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   cudaStream_t st = ex.st;
   static const char* const fwd_names[] = {"fwd_x", "fwd_x_div", "fwd_x_resid", "fwd_x_gradt"};
   PP_TRY_N(fwd_names[mode], (launch_fwd_x<T, TI>(ex.pl->g, ex.dt, ex.pl->fm, mode, args, spec, st)));
-  return spectral_core<T>(ex, spec, gauge);
+  PP_TRY_N("fft_z_fwd", launch_fft_z<T>(ex.pl->g, ex.dt, ex.pl->fz, -1, spec, st));
+  return spectral_mid<T>(ex, spec, gauge);
 }
 
+// Inverse z- and x-transforms of the spectral buffer into `out` with the epilogue `mode`.
 template <typename T, typename TO>
 poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate, PairArgs pair = PairArgs{nullptr, nullptr}) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   const double scale = 1.0 / ((double)ex.pl->g.nx * (double)ex.pl->g.nz);
   cudaStream_t st = ex.st;
   static const char* const inv_names[] = {"inv_x", "inv_x_accum", "inv_x_final"};
+  PP_TRY_N("fft_z_inv", launch_fft_z<T>(ex.pl->g, ex.dt, ex.pl->fz, +1, spec, st));
   PP_TRY_N(inv_names[mode], (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st,
                                                  pair)));
   return PS_OK;

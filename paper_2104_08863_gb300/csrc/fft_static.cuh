@@ -139,6 +139,40 @@ __device__ __forceinline__ void stage_inplace(cplx<T>* buf, const cplx<T>* __res
   __syncthreads();
 }
 
+// The first stage (span 1, no twiddles) with its inputs taken from load(t, n), element n of
+// transform t, instead of buf: the callers read a staged copy of the raw input and pack or
+// convert it on the way in, which saves one pass through shared memory.
+template <typename T, int L, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR, typename Load>
+__device__ __forceinline__ void stage_first(cplx<T>* buf, Load load) {
+  constexpr Radix F = factorize(L, MAXR);
+  constexpr int R = F.r[0];
+  constexpr int NBF = L / R;
+  constexpr int TOTAL = NBF * B;
+  constexpr int PER = (TOTAL + THREADS - 1) / THREADS;
+  cplx<T> v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * THREADS;
+    const int t = MAPB ? idx % B : idx / NBF, j = MAPB ? idx / B : idx % NBF;
+    if (TOTAL % THREADS == 0 || idx < TOTAL) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = load(t, j + r * NBF);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * THREADS;
+    const int t = MAPB ? idx % B : idx / NBF, j = MAPB ? idx / B : idx % NBF;
+    if (TOTAL % THREADS == 0 || idx < TOTAL) {
+      dft_r<T, R, SIGN>(v[q]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[padi<T>(t * BS + (j * R + r) * ES)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T, int L, int S, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR>
 __device__ __forceinline__ void stages_from(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   constexpr Radix F = factorize(L, MAXR);
@@ -154,6 +188,18 @@ template <typename T, int L, int SIGN, int B, int THREADS, int ES, int BS, bool 
 __device__ __forceinline__ void fft_static(cplx<T>* buf, const cplx<T>* __restrict__ tw) {
   static_assert(factorizable(L), "FFT length must be 2^a 3^b");
   stages_from<T, L, 0, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, tw);
+}
+
+// Full transform whose input is read by load(t, n) (see stage_first); `after_first()` runs once
+// every thread has finished reading the input (the staging it came from may then be refilled).
+template <typename T, int L, int SIGN, int B, int THREADS, int ES, int BS, bool MAPB, int MAXR, typename Load,
+          typename Hook>
+__device__ __forceinline__ void fft_static_from(cplx<T>* buf, const cplx<T>* __restrict__ tw, Load load,
+                                                Hook after_first) {
+  static_assert(factorizable(L), "FFT length must be 2^a 3^b");
+  stage_first<T, L, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, load);
+  after_first();
+  stages_from<T, L, 1, SIGN, B, THREADS, ES, BS, MAPB, MAXR>(buf, tw);
 }
 
 }  // namespace pp

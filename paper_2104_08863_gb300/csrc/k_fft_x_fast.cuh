@@ -8,6 +8,10 @@
 // 8 (FP64) staged complex values per stage.
 #pragma once
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fft_static.cuh"
 #include "xline.cuh"
 
@@ -186,6 +190,106 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
   }
 }
 
+// ---- persistent forward x-transform with the next tile's input in flight -------------------
+// A CTA walks tiles b, b + gridDim.x, ...; each tile's input lines are one contiguous stretch,
+// copied into a shared-memory staging area with 16-byte asynchronous copies (L2 only).  The
+// first FFT stage reads the staging area directly (packing or converting on the way), after
+// which the copy of the next tile is issued, so it travels while this tile is transformed and
+// stored.  The arithmetic is that of the single-tile kernels above.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from gmem to smem by the whole CTA.
+template <int THREADS>
+__device__ __forceinline__ void copy_async(void* smem, const void* gmem, size_t bytes) {
+  const int n = (int)(bytes >> 4);
+  for (int c = threadIdx.x; c < n; c += THREADS)
+    cp_async16(static_cast<char*>(smem) + 16 * (size_t)c, static_cast<const char*>(gmem) + 16 * (size_t)c);
+  cp_async_commit();
+}
+
+template <typename TI, int M> struct XPipe {
+  using X = XTile<float, M>;
+  static constexpr int LPB = X::LPB, THREADS = X::THREADS;
+  static constexpr int STAGE = LPB * 2 * M * (int)sizeof(TI);   // raw input lines
+  static constexpr int SMEM = STAGE + padded_size<float>(LPB * M) * (int)sizeof(cplx<float>);
+  static constexpr int MINB = 768 / THREADS > 0 ? 768 / THREADS : 1;   // <= 85 registers per thread
+};
+
+// Forward x-transform of a plain real field into the FP32 half spectrum.
+template <typename TI, int M>
+__global__ void __launch_bounds__(XPipe<TI, M>::THREADS, XPipe<TI, M>::MINB)
+    k_fwd_x_pipe(Geometry g, FwdArgs args, Tables<float> tt, cplx<float>* __restrict__ spec, int nlines) {
+  using C = XPipe<TI, M>;
+  constexpr int LPB = C::LPB, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TI* stage = reinterpret_cast<const TI*>(smem_raw);
+  cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw + C::STAGE);
+  const TI* in = reinterpret_cast<const TI*>(args.in);
+  const TI sc = TI(args.in_scale);
+  const int ntiles = (nlines + LPB - 1) / LPB;
+  auto issue = [&](int b) {
+    const int l0 = b * LPB;
+    copy_async<THREADS>(smem_raw, in + (size_t)l0 * g.nx, (size_t)min(LPB, nlines - l0) * g.nx * sizeof(TI));
+  };
+  if (blockIdx.x < ntiles) issue(blockIdx.x);
+  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+    const int line0 = b * LPB, nl = min(LPB, nlines - line0);
+    cp_async_wait_all();
+    __syncthreads();
+    auto load = [&](int t, int n) -> cplx<float> {
+      if (t >= nl) return mk<float>(0.f, 0.f);
+      if constexpr (sizeof(TI) == 8) {
+        const double2 v = *reinterpret_cast<const double2*>(stage + (size_t)t * g.nx + 2 * n);
+        return mk<float>(f64_to_f32_trunc(v.x), f64_to_f32_trunc(v.y));
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(stage + (size_t)t * g.nx + 2 * n);
+        return mk<float>(float(v.x * sc), float(v.y * sc));
+      }
+    };
+    auto refill = [&]() {
+      if (b + (int)gridDim.x < ntiles) issue(b + gridDim.x);
+    };
+    fft_static_from<float, M, -1, LPB, THREADS, 1, M, false, XTile<float, M>::MAXR>(buf, tt.tw_m, load, refill);
+    constexpr int M1 = M + 1;
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
+      const int t = idx / M1, kx = idx % M1;
+      if (t >= nl) continue;
+      const cplx<float> Zk = buf[padi<float>(t * M + (kx == M ? 0 : kx))];
+      const cplx<float> Zc = conj(buf[padi<float>(t * M + (kx == 0 ? 0 : M - kx))]);
+      st_c(spec + (size_t)(line0 + t) * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+    }
+  }
+}
+
+// Resident CTAs of a kernel on the whole GPU (queried once per kernel and shared-memory size).
+template <typename K>
+inline cudaError_t resident_grid(K kernel, int threads, int smem, int& grid) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  cudaError_t e = ensure_smem_limit((const void*)kernel, (size_t)smem);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair((const void*)kernel, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) { grid = it->second; return cudaSuccess; }
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, (size_t)smem)) != cudaSuccess)
+    return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  grid = sms * per;
+  cache[key] = grid;
+  return cudaSuccess;
+}
+
 template <typename K>
 inline cudaError_t set_smem(K kernel, int smem) {
   return ensure_smem_limit((const void*)kernel, (size_t)smem);
@@ -203,6 +307,19 @@ cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<
     auto k = k_fwd_x_fast<T, TI, M, MODEV>;                                             \
     if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                            \
     k<<<grid, C::THREADS, C::SMEM, st>>>(g, args, tt, tb, spec, nlines);                \
+  }
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8) {
+    // FP64 right-hand side into the FP32 spectrum: the input is the widest stream of the solve,
+    // and keeping the next tile's lines in flight pays for the smaller CTA count
+    if (mode == FWD_PLAIN) {
+      using P = XPipe<TI, M>;
+      auto k = k_fwd_x_pipe<TI, M>;
+      int rg = 0;
+      if ((e = resident_grid(k, P::THREADS, P::SMEM, rg)) != cudaSuccess) return e;
+      const int ntiles = (nlines + P::LPB - 1) / P::LPB;
+      k<<<rg < ntiles ? rg : ntiles, P::THREADS, P::SMEM, st>>>(g, args, tt, spec, nlines);
+      return cudaGetLastError();
+    }
   }
   if constexpr (sizeof(T) == sizeof(TI)) {
     switch (mode) {
