@@ -601,6 +601,8 @@ PROFILE_CASES = {
     # the full 1536 x 1024 planes of the precision form at 64 rows (a fifth entry would add plan flags)
     "fp32_refined_solve_1536x64x1024": (W.ChannelCase("channel_1536x64x1024_tanh2.2", 1536, 64, 1024, 2.2), 2, 1,
                                         "solve"),
+    # the precision form itself (launch lists only: one metric pass)
+    "fp32_refined_solve_1536x768x1024": (W.CHANNEL_1536, 2, 1, "solve"),
 }
 
 
