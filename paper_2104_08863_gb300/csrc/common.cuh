@@ -43,6 +43,6 @@ template <typename T> __device__ __forceinline__ void st_c(cplx<T>* p, cplx<T> a
 }
 
 // Device status word codes (mirror poisson_status).
-enum : int { DEV_OK = 0, DEV_NONFINITE = 6 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 5, DEV_NONFINITE = 6 };
 
 }  // namespace pp

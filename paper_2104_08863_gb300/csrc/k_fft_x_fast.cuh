@@ -192,25 +192,45 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
 
 // ---- persistent forward x-transform with the next tile's input in flight -------------------
 // A CTA walks tiles b, b + gridDim.x, ...; each tile's input lines are one contiguous stretch,
-// copied into a shared-memory staging area with 16-byte asynchronous copies (L2 only).  The
-// first FFT stage reads the staging area directly (packing or converting on the way), after
-// which the copy of the next tile is issued, so it travels while this tile is transformed and
-// stored.  The arithmetic is that of the single-tile kernels above.
+// which one thread copies into a shared-memory staging area with a single bulk asynchronous copy
+// (the TMA engine, completion counted in bytes on an mbarrier).  The first FFT stage reads the
+// staging area directly (packing or converting on the way), after which the copy of the next tile
+// is issued, so it travels while this tile is transformed and stored.  The arithmetic is that of
+// the single-tile kernels above.
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// bytes (a multiple of 16, both addresses 16-byte aligned) from gmem to smem by the whole CTA.
-template <int THREADS>
-__device__ __forceinline__ void copy_async(void* smem, const void* gmem, size_t bytes) {
-  const int n = (int)(bytes >> 4);
-  for (int c = threadIdx.x; c < n; c += THREADS)
-    cp_async16(static_cast<char*>(smem) + 16 * (size_t)c, static_cast<const char*>(gmem) + 16 * (size_t)c);
-  cp_async_commit();
+// Thread 0: `bytes` (a multiple of 16; both addresses 16-byte aligned) from gmem to smem, counted
+// on bar.  The proxy fence orders the CTA's earlier generic reads of the destination (made
+// visible to thread 0 by a barrier) before the asynchronous write.
+__device__ __forceinline__ void bulk_load(void* smem, const void* gmem, unsigned bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(smem)),
+               "l"(gmem), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of bar; false after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned it = 0; it < (1u << 26); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 32)) return false;
+  }
+  return false;
 }
 
 template <typename TI, int M> struct XPipe {
@@ -224,24 +244,34 @@ template <typename TI, int M> struct XPipe {
 // Forward x-transform of a plain real field into the FP32 half spectrum.
 template <typename TI, int M>
 __global__ void __launch_bounds__(XPipe<TI, M>::THREADS, XPipe<TI, M>::MINB)
-    k_fwd_x_pipe(Geometry g, FwdArgs args, Tables<float> tt, cplx<float>* __restrict__ spec, int nlines) {
+    k_fwd_x_pipe(Geometry g, FwdArgs args, Tables<float> tt, cplx<float>* __restrict__ spec, int lbeg, int nlines,
+                 int* status) {
   using C = XPipe<TI, M>;
   constexpr int LPB = C::LPB, THREADS = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const TI* stage = reinterpret_cast<const TI*>(smem_raw);
-  cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw + C::STAGE);
+  extern __shared__ __align__(128) unsigned char xpipe_smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const TI* stage = reinterpret_cast<const TI*>(xpipe_smem);
+  cplx<float>* buf = reinterpret_cast<cplx<float>*>(xpipe_smem + C::STAGE);
   const TI* in = reinterpret_cast<const TI*>(args.in);
   const TI sc = TI(args.in_scale);
-  const int ntiles = (nlines + LPB - 1) / LPB;
+  const int ntiles = (nlines - lbeg + LPB - 1) / LPB;
   auto issue = [&](int b) {
-    const int l0 = b * LPB;
-    copy_async<THREADS>(smem_raw, in + (size_t)l0 * g.nx, (size_t)min(LPB, nlines - l0) * g.nx * sizeof(TI));
+    if (threadIdx.x == 0) {
+      const int l0 = lbeg + b * LPB;
+      bulk_load(xpipe_smem, in + (size_t)l0 * g.nx, (unsigned)((size_t)min(LPB, nlines - l0) * g.nx * sizeof(TI)), &bar);
+    }
   };
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
   if (blockIdx.x < ntiles) issue(blockIdx.x);
-  for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
-    const int line0 = b * LPB, nl = min(LPB, nlines - line0);
-    cp_async_wait_all();
-    __syncthreads();
+  unsigned parity = 0;
+  for (int b = blockIdx.x; b < ntiles; b += gridDim.x, parity ^= 1u) {
+    const int line0 = lbeg + b * LPB, nl = min(LPB, nlines - line0);
+    // the tile has landed (or, uniformly for the CTA, the bounded wait gave up)
+    if (!__syncthreads_and(mbar_wait(&bar, parity))) {
+      if (threadIdx.x == 0) atomicExch(status, (int)DEV_TIMEOUT);
+      return;
+    }
     auto load = [&](int t, int n) -> cplx<float> {
       if (t >= nl) return mk<float>(0.f, 0.f);
       if constexpr (sizeof(TI) == 8) {
@@ -308,16 +338,17 @@ cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<
     if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                            \
     k<<<grid, C::THREADS, C::SMEM, st>>>(g, args, tt, tb, spec, nlines);                \
   }
-  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8) {
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8 && M >= 256) {
     // FP64 right-hand side into the FP32 spectrum: the input is the widest stream of the solve,
-    // and keeping the next tile's lines in flight pays for the smaller CTA count
+    // and keeping the next tile's lines in flight pays for the smaller CTA count (long lines:
+    // tiles of 2-8 lines, no register spills)
     if (mode == FWD_PLAIN) {
       using P = XPipe<TI, M>;
       auto k = k_fwd_x_pipe<TI, M>;
       int rg = 0;
       if ((e = resident_grid(k, P::THREADS, P::SMEM, rg)) != cudaSuccess) return e;
       const int ntiles = (nlines + P::LPB - 1) / P::LPB;
-      k<<<rg < ntiles ? rg : ntiles, P::THREADS, P::SMEM, st>>>(g, args, tt, spec, nlines);
+      k<<<rg < ntiles ? rg : ntiles, P::THREADS, P::SMEM, st>>>(g, args, tt, spec, 0, nlines, tb.status);
       return cudaGetLastError();
     }
   }
