@@ -48,9 +48,20 @@ __host__ __device__ __forceinline__ float float_of(uint32_t u) {
   return x;
 }
 
+// Normal range of the fast paths: biased FP64 exponent e with e - 896 a normal FP32 exponent
+// (truncation), and in addition e - 948 one (the scale of the split's low part).  There the FP32
+// bits are the top 32 bits of u << 3 with the exponent field rebiased by -896 (mod 512, which the
+// 9-bit field after the shift absorbs) and the sign put back.
+__host__ __device__ __forceinline__ float f64_hi_fast(uint32_t h, uint32_t l) {
+  const uint32_t t = ((h << 3) | (l >> 29)) - (384u << 23);
+  return float_of((t & 0x7fffffffu) | (h & 0x80000000u));
+}
+
 // x truncated toward zero to FP32 (flush below the normal range, +-inf above it).
 __host__ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   const uint64_t u = bits_of(x);
+  const uint32_t h = (uint32_t)(u >> 32);
+  if (((h >> 20) & 0x7ffu) - 897u <= 1150u - 897u) return f64_hi_fast(h, (uint32_t)u);
   const uint32_t sign = (uint32_t)(u >> 63) << 31;
   const int e = (int)((u >> 52) & 0x7ff);
   if (e == 0x7ff) return float_of(sign | 0x7f800000u | ((u & 0xfffffffffffffull) ? 0x400000u : 0u));
@@ -62,8 +73,18 @@ __host__ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 
 // hi = f64_to_f32_trunc(x), lo ~= x - hi (the remaining 29 significand bits, rounded to 24).
 __host__ __device__ __forceinline__ void f64_split(double x, float& hi, float& lo) {
-  hi = f64_to_f32_trunc(x);
   const uint64_t u = bits_of(x);
+  {
+    const uint32_t h = (uint32_t)(u >> 32), l = (uint32_t)u;
+    const uint32_t e = (h >> 20) & 0x7ffu;
+    if (e - 949u <= 1150u - 949u) {
+      hi = f64_hi_fast(h, l);
+      const float mag = (float)(l & 0x1fffffffu) * float_of((e - 948u) << 23);
+      lo = float_of(bits_of(mag) | (h & 0x80000000u));
+      return;
+    }
+  }
+  hi = f64_to_f32_trunc(x);
   const int e = (int)((u >> 52) & 0x7ff);
   const int se = e - 1075 + 127;   // exponent of one unit of the remainder
   const int fe = e - 1023 + 127;
