@@ -273,6 +273,17 @@ __device__ __forceinline__ void dot2_sub(float& S, float& C, df coef, df d) {
 
 __device__ __forceinline__ float2 ld_f2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
+// a + b of two double-float differences: hi parts by TwoSum, low parts added (unnormalised;
+// the error is ~2^-48 of the larger difference, not of the pressure values).
+__device__ __forceinline__ df diff_sum(df a, df b) {
+  const df s = two_sum_df(a.hi, b.hi);
+  return df{s.hi, s.lo + (a.lo + b.lo)};
+}
+
+// Per cell: the neighbour differences of p = hi + lo, each exact (TwoDiff of the hi values, plus
+// TwoDiff of the lo values added by diff_sum), grouped by coefficient (x: both neighbours, z:
+// both neighbours, y: one per face), so that each group costs one compensated product; the
+// difference between the two cells of the pair is shared.
 __device__ __forceinline__ float2 resid_pair_line(const ResidLine& R, int n) {
   const int i0 = 2 * n;
   const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
@@ -294,31 +305,33 @@ __device__ __forceinline__ float2 resid_pair_line(const ResidLine& R, int n) {
     if (R.Qym) qym = ld_f2(R.Qym + i0);
     if (R.Qyp) qyp = ld_f2(R.Qyp + i0);
   }
+  // p at cell 1 minus p at cell 0 (x-neighbours of each other)
+  df d01 = two_diff_df(pc.y, pc.x);
+  if (R.Q) d01 = diff_sum(d01, two_diff_df(qc.y, qc.x));
   float out[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const float ctr = c ? pc.y : pc.x;
-    const float xl = c ? pc.x : pm, xr = c ? pp : pc.y;
     float fh, fl;
     f64_split(c ? fv.y : fv.x, fh, fl);
     const df s0 = two_sum_df(fh, -R.mh);
     float S = s0.hi, C = s0.lo + (fl - R.ml);
-    dot2_sub(S, C, R.cx, two_diff_df(xr, ctr));
-    dot2_sub(S, C, R.cx, two_diff_df(xl, ctr));
-    dot2_sub(S, C, R.cz, two_diff_df(c ? zp.y : zp.x, ctr));
-    dot2_sub(S, C, R.cz, two_diff_df(c ? zm.y : zm.x, ctr));
-    if (R.Pym) dot2_sub(S, C, R.ca, two_diff_df(c ? ym.y : ym.x, ctr));
-    if (R.Pyp) dot2_sub(S, C, R.cc, two_diff_df(c ? yp.y : yp.x, ctr));
+    // x: (p_{i+1} - p_i) + (p_{i-1} - p_i), one of them the shared d01
+    df dout = c ? two_diff_df(pp, ctr) : two_diff_df(pm, ctr);
+    df dz0 = two_diff_df(c ? zp.y : zp.x, ctr), dz1 = two_diff_df(c ? zm.y : zm.x, ctr);
+    df dy0 = two_diff_df(c ? ym.y : ym.x, ctr), dy1 = two_diff_df(c ? yp.y : yp.x, ctr);
     if (R.Q) {
       const float qctr = c ? qc.y : qc.x;
-      const float qxl = c ? qc.x : qm, qxr = c ? qp : qc.y;
-      dot2_sub(S, C, R.cx, two_diff_df(qxr, qctr));
-      dot2_sub(S, C, R.cx, two_diff_df(qxl, qctr));
-      dot2_sub(S, C, R.cz, two_diff_df(c ? qzp.y : qzp.x, qctr));
-      dot2_sub(S, C, R.cz, two_diff_df(c ? qzm.y : qzm.x, qctr));
-      if (R.Qym) dot2_sub(S, C, R.ca, two_diff_df(c ? qym.y : qym.x, qctr));
-      if (R.Qyp) dot2_sub(S, C, R.cc, two_diff_df(c ? qyp.y : qyp.x, qctr));
+      dout = diff_sum(dout, c ? two_diff_df(qp, qctr) : two_diff_df(qm, qctr));
+      dz0 = diff_sum(dz0, two_diff_df(c ? qzp.y : qzp.x, qctr));
+      dz1 = diff_sum(dz1, two_diff_df(c ? qzm.y : qzm.x, qctr));
+      if (R.Qym) dy0 = diff_sum(dy0, two_diff_df(c ? qym.y : qym.x, qctr));
+      if (R.Qyp) dy1 = diff_sum(dy1, two_diff_df(c ? qyp.y : qyp.x, qctr));
     }
+    dot2_sub(S, C, R.cx, diff_sum(dout, c ? df_neg(d01) : d01));
+    dot2_sub(S, C, R.cz, diff_sum(dz0, dz1));
+    if (R.Pym) dot2_sub(S, C, R.ca, dy0);
+    if (R.Pyp) dot2_sub(S, C, R.cc, dy1);
     out[c] = S + C;
   }
   return make_float2(out[0], out[1]);
