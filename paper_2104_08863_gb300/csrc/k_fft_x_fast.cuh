@@ -338,10 +338,11 @@ cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<
     if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                            \
     k<<<grid, C::THREADS, C::SMEM, st>>>(g, args, tt, tb, spec, nlines);                \
   }
-  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8 && M >= 256) {
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8 && M >= 256 && M != 384) {
     // FP64 right-hand side into the FP32 spectrum: the input is the widest stream of the solve,
     // and keeping the next tile's lines in flight pays for the smaller CTA count (long lines:
-    // tiles of 2-8 lines, no register spills)
+    // tiles of 2-8 lines; Nx/2 = 384 spills and keeps the single-tile kernel; FP32 inputs, half
+    // as wide, measured faster with the single-tile kernel)
     if (mode == FWD_PLAIN) {
       using P = XPipe<TI, M>;
       auto k = k_fwd_x_pipe<TI, M>;
