@@ -713,55 +713,6 @@ poisson_status projection_step_adjoint(poisson_plan_t pl, void* gu, void* gv, vo
   return PS_OK;
 }
 
-}  // extern "C"
-
-namespace {
-
-// Host <-> device copies of several buffers in pieces of at most 64 MB spread round-robin over
-// the plan's copy streams, so that several copy engines move data at once; the pieces start after
-// the work already on `st` and `st` waits for all of them.
-struct Copy {
-  void* dst;
-  const void* src;
-  size_t bytes;
-};
-constexpr int kCopyStreams = 4;
-
-poisson_status copy_spread(poisson_plan_s* pl, const Copy* cp, int n, cudaMemcpyKind kind, cudaStream_t st) {
-  while ((int)pl->copy_streams.size() < kCopyStreams) {
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PS_ECUDA;
-    pl->copy_streams.push_back(s);
-  }
-  while ((int)pl->copy_events.size() < kCopyStreams + 1) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PS_ECUDA;
-    pl->copy_events.push_back(e);
-  }
-  if (cudaEventRecord(pl->copy_events[kCopyStreams], st) != cudaSuccess) return PS_ECUDA;
-  for (int q = 0; q < kCopyStreams; ++q)
-    if (cudaStreamWaitEvent(pl->copy_streams[q], pl->copy_events[kCopyStreams], 0) != cudaSuccess) return PS_ECUDA;
-  const size_t piece = (size_t)64 << 20;
-  int next = 0;
-  for (int b = 0; b < n; ++b)
-    for (size_t off = 0; off < cp[b].bytes; off += piece) {
-      const size_t len = cp[b].bytes - off < piece ? cp[b].bytes - off : piece;
-      if (cudaMemcpyAsync((char*)cp[b].dst + off, (const char*)cp[b].src + off, len, kind,
-                          pl->copy_streams[next]) != cudaSuccess)
-        return PS_ECUDA;
-      next = (next + 1) % kCopyStreams;
-    }
-  for (int q = 0; q < kCopyStreams; ++q) {
-    if (cudaEventRecord(pl->copy_events[q], pl->copy_streams[q]) != cudaSuccess) return PS_ECUDA;
-    if (cudaStreamWaitEvent(st, pl->copy_events[q], 0) != cudaSuccess) return PS_ECUDA;
-  }
-  return PS_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
 poisson_status projection_step_host(poisson_plan_t pl, void* u_h, void* v_h, void* w_h, void* p_h, void* u_d,
                                     void* v_d, void* w_d, void* p_d, double dt, void* stream) {
   if (!pl || !u_h || !v_h || !w_h || !u_d || !v_d || !w_d) return PS_EINVAL;
@@ -770,11 +721,14 @@ poisson_status projection_step_host(poisson_plan_t pl, void* u_h, void* v_h, voi
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = pl->precision == PP_FP64 ? 8 : 4;
   const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
-  const Copy in[3] = {{u_d, u_h, nc}, {v_d, v_h, nv}, {w_d, w_h, nc}};
-  PP_RET(copy_spread(pl, in, 3, cudaMemcpyHostToDevice, st));
+  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   PP_RET(projection_step(pl, u_d, v_d, w_d, p_h ? p_d : nullptr, dt, stream));
-  const Copy outc[4] = {{u_h, u_d, nc}, {v_h, v_d, nv}, {w_h, w_d, nc}, {p_h, p_d, p_h ? nc : 0}};
-  PP_RET(copy_spread(pl, outc, 4, cudaMemcpyDeviceToHost, st));
+  if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (p_h && cudaMemcpyAsync(p_h, p_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
   return PS_OK;
 }
@@ -788,11 +742,14 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = pl->precision == PP_FP32 ? 4 : 8;
   const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
-  const Copy in[3] = {{u_d, u_h, nc}, {v_d, v_h, nv}, {w_d, w_h, nc}};
-  PP_RET(copy_spread(pl, in, 3, cudaMemcpyHostToDevice, st));
+  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
-  const Copy outc[4] = {{u_h, u_d, nc}, {v_h, v_d, nv}, {w_h, w_d, nc}, {p_h, p_d, p_h ? nc : 0}};
-  PP_RET(copy_spread(pl, outc, 4, cudaMemcpyDeviceToHost, st));
+  if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
+  if (p_h && cudaMemcpyAsync(p_h, p_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
   return PS_OK;
 }
@@ -828,8 +785,6 @@ int poisson_stage_times(poisson_plan_t pl, float* ms, const char** names, int ma
 poisson_status poisson_plan_destroy(poisson_plan_t pl) {
   if (pl) {
     for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : pl->copy_events) cudaEventDestroy(e);
-    for (cudaStream_t c : pl->copy_streams) cudaStreamDestroy(c);
     pp::destroy_batch(pl);
   }
   delete pl;

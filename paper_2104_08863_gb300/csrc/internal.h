@@ -231,9 +231,6 @@ struct poisson_plan_s {
   std::vector<cudaEvent_t> ev;
   std::vector<const char*> ev_names;
   int nev;
-  // host entry points: copy streams (several copy engines at once) and their fork/join events
-  std::vector<cudaStream_t> copy_streams;
-  std::vector<cudaEvent_t> copy_events;
   // batched plans (poisson_plan_batched): sub-plans, fork streams and the cached graph
   std::vector<poisson_plan_s*> children;
   std::vector<cudaStream_t> forks;
