@@ -264,3 +264,19 @@ def test_fp32_truncated_pdd_matches_oracle_truncated(P, parts):
                   fp64_low_modes=L, device=DEV)
     got = solve_gpu(P, plan, f, dtype=torch.float32)
     assert relerr(got, want) <= 2e-5
+
+
+def test_fp32_refined_solve_ragged_staged_tiles(P):
+    """Nx/2 = 256 takes the x-transform whose FP64 right-hand side is staged by bulk copies, tiles
+    of 8 lines: 3 x 18 = 54 lines leave a ragged last tile."""
+    nx, ny, nz = 512, 3, 18
+    faces = W.tanh_faces(ny, 1.6)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(5, nx, ny, nz))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=1, fp64_low_modes=4, refine_steps=2,
+                  device=DEV)
+    got = plan.solve(to_dev(f))
+    torch.cuda.synchronize()
+    assert relerr(got.cpu().numpy(), want) <= 1e-12
+    assert plan.device_status() == 0
