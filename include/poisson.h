@@ -68,6 +68,11 @@ typedef enum {
 #define POISSON_TIMING       0x2u   /* flag: record CUDA events around every kernel launch */
 #define POISSON_GENERIC_FFT  0x4u   /* flag: use the runtime-generic FFT kernels instead of the
                                        compile-time specialised ones (a tiling the autotuner tries) */
+#define POISSON_SELFTEST_WAIT 0x8u  /* diagnostics flag: the x-transform that stages its FP64
+                                       input by bulk copies (FP32 plans, Nx/2 >= 256) skips its
+                                       first copy, so its bounded wait runs out (~2 s): the call
+                                       returns, the result is undefined and the device status
+                                       reads PS_ETIMEOUT.  For testing the failure path only.  */
 
 typedef struct {
   int nx, ny, nz;           /* cells; nx even, nx/2 and nz of the form 2^a 3^b; ny >= 2 */

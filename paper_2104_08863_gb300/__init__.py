@@ -14,10 +14,12 @@ import torch
 
 from . import _native
 from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_PDD_EXACT, PT_PDD_TRUNCATED,
-                      POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, PoissonError, check)
+                      POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, POISSON_SELFTEST_WAIT, PoissonError,
+                      check)
 
 __all__ = ["Plan", "BatchPlan", "autotune", "tune_batch", "ProjectionFn", "PoissonError", "POISSON_GENERIC_FFT", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
-           "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "PT_PDD_TRUNCATED", "POISSON_CHECK_FINITE", "POISSON_TIMING"]
+           "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "PT_PDD_TRUNCATED", "POISSON_CHECK_FINITE", "POISSON_TIMING",
+           "POISSON_SELFTEST_WAIT"]
 
 
 def _ptr(t: torch.Tensor) -> int:

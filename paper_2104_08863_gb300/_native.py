@@ -19,6 +19,7 @@ POISSON_STATIC_WS_MAX_BYTES = 8 * 1024 * 1024
 POISSON_CHECK_FINITE = 0x1
 POISSON_TIMING = 0x2
 POISSON_GENERIC_FFT = 0x4
+POISSON_SELFTEST_WAIT = 0x8
 
 # Every symbol declared in include/poisson.h.
 EXPORTS = (

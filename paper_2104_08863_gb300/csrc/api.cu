@@ -174,6 +174,7 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   g.dx = d->lx / d->nx;
   g.dz = d->lz / d->nz;
   g.generic_fft = (d->flags & POISSON_GENERIC_FFT) ? 1 : 0;
+  g.selftest_wait = (d->flags & POISSON_SELFTEST_WAIT) ? 1 : 0;
   pl->lx = d->lx; pl->lz = d->lz;
   pl->precision = d->precision;
   pl->tridiag = d->tridiag;

@@ -53,6 +53,7 @@ struct Geometry {
   int nx, ny, nz, M, ncols, pitch;
   double dx, dz;
   int generic_fft;   // 1: use the runtime-generic FFT kernels (POISSON_GENERIC_FFT)
+  int selftest_wait; // 1: the bulk-copy-staged x-transform skips its first copy (POISSON_SELFTEST_WAIT)
 };
 
 struct LaunchCount {

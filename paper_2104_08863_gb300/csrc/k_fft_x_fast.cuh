@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(XPipe<TI, M>::THREADS, XPipe<TI, M>::MINB)
   };
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
-  if (blockIdx.x < ntiles) issue(blockIdx.x);
+  if (blockIdx.x < ntiles && !g.selftest_wait) issue(blockIdx.x);
   unsigned parity = 0;
   for (int b = blockIdx.x; b < ntiles; b += gridDim.x, parity ^= 1u) {
     const int line0 = lbeg + b * LPB, nl = min(LPB, nlines - line0);

@@ -280,3 +280,25 @@ def test_fp32_refined_solve_ragged_staged_tiles(P):
     torch.cuda.synchronize()
     assert relerr(got.cpu().numpy(), want) <= 1e-12
     assert plan.device_status() == 0
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(P):
+    """POISSON_SELFTEST_WAIT makes the bulk-copy-staged x-transform skip its first copy: its
+    bounded mbarrier wait gives up (~2 s), the device status reads PS_ETIMEOUT, and the context
+    stays usable for the next solve."""
+    from paper_2104_08863_gb300 import _native
+    nx, ny, nz = 512, 4, 16
+    faces = W.tanh_faces(ny, 1.5)
+    f = np.random.default_rng(9).standard_normal((ny, nz, nx))
+    bad = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=1, flags=P.POISSON_SELFTEST_WAIT,
+                 device=DEV)
+    bad.solve(to_dev(f))
+    torch.cuda.synchronize()
+    assert bad.device_status() == _native.PS_ETIMEOUT
+    g = oracle.Grid(nx, nz, faces)
+    f -= np.einsum("j,jki->", g.dy, f) / (g.dy.sum() * nx * nz)
+    good = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=1, refine_steps=2, device=DEV)
+    got = good.solve(to_dev(f))
+    torch.cuda.synchronize()
+    assert good.device_status() == 0
+    assert relerr(got.cpu().numpy(), oracle.solve(g, f)) <= 1e-12
