@@ -106,6 +106,14 @@ poisson_status poisson_set_workspace(poisson_plan_t plan, void* workspace, size_
  * rhs == p (in place) is allowed. */
 poisson_status poisson_solve(poisson_plan_t plan, const void* rhs, void* p, void* stream);
 
+/* The transpose of poisson_solve as a linear map of rhs (its adjoint, for gradient-based
+ * callers): q = S^T g.  Computed as W S(W^-1 g) with W = diag(dy_j) (L_h^T = W L_h W^-1, and the
+ * removal of the rhs mean and the zero-mean gauge of S transpose into each other), so q solves
+ * L_h^T q = g - omega sum(g) (omega_j = dy_j / (nx nz sum dy)) with sum(q) = 0.
+ * g, q: device [ny][nz][nx] with the dtype of poisson_solve; g == q is allowed.  With
+ * PP_FP32_REFINED the workspace's pressure pair is overwritten.  Errors as for poisson_solve. */
+poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* g, void* q, void* stream);
+
 /* One projection (Eqs. 4 and 7): p solves L_h p = D(u_star) / dt (made compatible), then
  * u = u_star - dt G p in place on u, v, w.  The wall faces of v are boundary values: they enter D
  * and are not modified.  p_out (device [ny][nz][nx], may be NULL) receives p.

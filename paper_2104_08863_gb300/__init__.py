@@ -85,6 +85,16 @@ class Plan:
         check(_native.lib().poisson_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "poisson_solve")
         return out
 
+    def solve_adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """q = S^T g, the transpose of ``solve`` as a linear map (g is not modified unless out is g)."""
+        self._check(g, self.cell_shape, "g")
+        if out is None:
+            out = torch.empty_like(g)
+        self._check(out, self.cell_shape, "out")
+        check(_native.lib().poisson_solve_adjoint(self._h, _ptr(g), _ptr(out), _stream(stream)),
+              "poisson_solve_adjoint")
+        return out
+
     def project(self, u, v, w, dt: float, p_out=None, stream=None):
         """In-place projection of (u, v, w); returns p_out (or None)."""
         self._check(u, self.cell_shape, "u")

@@ -24,7 +24,7 @@ POISSON_SELFTEST_WAIT = 0x8
 # Every symbol declared in include/poisson.h.
 EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
-    "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
+    "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
     "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
     "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
     L.poisson_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.poisson_set_workspace.argtypes = [vp, vp, sz, vp]
     L.poisson_solve.argtypes = [vp, vp, vp, vp]
+    L.poisson_solve_adjoint.argtypes = [vp, vp, vp, vp]
     L.poisson_solve_static_ws.argtypes = [vp, vp, vp, vp]
     L.poisson_plan_batched.argtypes = [ctypes.POINTER(PoissonDesc), i, ctypes.POINTER(vp)]
     L.poisson_solve_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -83,7 +84,7 @@ def lib() -> ctypes.CDLL:
     L.poisson_status_string.argtypes = [i]
     L.poisson_status_string.restype = ctypes.c_char_p
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
-                 "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
+                 "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
                  "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
                  "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_plan_destroy"):
         getattr(L, name).restype = i

@@ -635,6 +635,37 @@ poisson_status poisson_solve(poisson_plan_t pl, const void* rhs, void* p, void* 
   return solve_impl(ex, rhs, p);
 }
 
+// S^T g for the gauged solve S of poisson_solve: since L_h^T = W L_h W^-1 (W = diag(dy_j)) and the
+// mean removal and the gauge of S transpose into each other, S^T g = W S(W^-1 g).
+poisson_status poisson_solve_adjoint(poisson_plan_t pl, const void* g, void* q, void* stream) {
+  if (!pl || !g || !q) return PS_EINVAL;
+  if (!pl->children.empty()) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!aligned16(g) || !aligned16(q)) return PS_EINVAL;
+  pl->launches = 0;
+  pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  const Geometry& geo = pl->g;
+  cudaStream_t st = ex.st;
+  if (pl->precision == PP_FP32) {
+    PP_TRY_N("scale_in", launch_scale_planes<float>(geo, ex.dt, (const float*)g, (float*)q, false, st));
+    PP_RET(solve_impl(ex, q, q));
+    PP_TRY_N("scale_out", launch_scale_planes<float>(geo, ex.dt, (const float*)q, (float*)q, true, st));
+  } else if (pl->precision == PP_FP64) {
+    PP_TRY_N("scale_in", launch_scale_planes<double>(geo, ex.dt, (const double*)g, (double*)q, false, st));
+    PP_RET(solve_impl(ex, q, q));
+    PP_TRY_N("scale_out", launch_scale_planes<double>(geo, ex.dt, (const double*)q, (double*)q, true, st));
+  } else {
+    // the refined solve re-reads its rhs: solve into the workspace's pressure pair, then weight it
+    PP_TRY_N("scale_in", launch_scale_planes<double>(geo, ex.dt, (const double*)g, (double*)q, false, st));
+    PP_RET(solve_impl(ex, q, nullptr, true));
+    const float* hi = (const float*)(ex.ws + pl->off_pbuf);
+    const float* lo = (const float*)(ex.ws + pl->off_pbuf2);
+    PP_TRY_N("weighted_pair", launch_weighted_pair(geo, ex.dt, hi, lo, (double*)q, st));
+  }
+  return PS_OK;
+}
+
 poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, void* p_out, double dt,
                                void* stream) {
   if (!pl || !u || !v || !w) return PS_EINVAL;

@@ -177,6 +177,13 @@ template <typename T>
 cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, const T* q, T* gu, T* gv, T* gw,
                                     cudaStream_t st);
 
+// out = in * (1/dy_j) or in * dy_j per y-plane j (in == out allowed), and q = dy_j (hi + lo) in FP64.
+template <typename T>
+cudaError_t launch_scale_planes(const Geometry& g, const DevTables& tb, const T* in, T* out, bool to_weighted,
+                                cudaStream_t st);
+cudaError_t launch_weighted_pair(const Geometry& g, const DevTables& tb, const float* hi, const float* lo, double* q,
+                                 cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st);
 

@@ -7,6 +7,7 @@
 //                L_h^T = W L_h W^-1 and the forward gauge (zero dy-weighted mean of p') is the
 //                zero-sum gauge of q.
 //  k_check_finite : sets the device status word when a value is NaN or Inf.
+#include "fpconv.cuh"
 #include "internal.h"
 
 namespace pp {
@@ -63,6 +64,33 @@ __global__ void __launch_bounds__(256) k_adj_epi(Geometry g, const T* __restrict
   }
 }
 
+// out[j][k][i] = in[j][k][i] * s_j with s_j = 1/dy_j (to_weighted = false) or dy_j (true): the
+// diagonal volume weights W^-1 and W of the transposed solve (L_h^T = W L_h W^-1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale_planes(Geometry g, const T* __restrict__ in, T* __restrict__ out,
+                                                      const double* __restrict__ dy, int to_weighted) {
+  const int nlines = g.ny * g.nz;
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
+    const int j = line / g.nz;
+    const T sj = to_weighted ? T(dy[j]) : T(1.0 / dy[j]);
+    const size_t base = (size_t)line * g.nx;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) out[base + i] = in[base + i] * sj;
+  }
+}
+
+// q[j][k][i] = dy_j (hi + lo): the FP64 value of the refined solve's FP32 pair, weighted.
+__global__ void __launch_bounds__(256) k_weighted_pair(Geometry g, const float* __restrict__ hi,
+                                                       const float* __restrict__ lo, double* __restrict__ q,
+                                                       const double* __restrict__ dy) {
+  const int nlines = g.ny * g.nz;
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
+    const double w = dy[line / g.nz];
+    const size_t base = (size_t)line * g.nx;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
+      q[base + i] = w * f32_sum_to_f64(hi[base + i], lo ? lo[base + i] : 0.0f);
+  }
+}
+
 template <typename T>
 __global__ void k_check_finite(const T* __restrict__ x, size_t n, int* status) {
   bool bad = false;
@@ -105,6 +133,21 @@ cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, cons
 }
 
 template <typename T>
+cudaError_t launch_scale_planes(const Geometry& g, const DevTables& tb, const T* in, T* out, bool to_weighted,
+                                cudaStream_t st) {
+  const int nlines = g.ny * g.nz, cap = 152 * 16;
+  k_scale_planes<T><<<nlines < cap ? nlines : cap, line_block(g), 0, st>>>(g, in, out, tb.dy, to_weighted ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_pair(const Geometry& g, const DevTables& tb, const float* hi, const float* lo, double* q,
+                                 cudaStream_t st) {
+  const int nlines = g.ny * g.nz, cap = 152 * 16;
+  k_weighted_pair<<<nlines < cap ? nlines : cap, line_block(g), 0, st>>>(g, hi, lo, q, tb.dy);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st) {
   k_check_finite<T><<<stream_grid(n), 256, 0, st>>>(x, n, status);
   return cudaGetLastError();
@@ -118,6 +161,10 @@ template cudaError_t launch_adjoint_epilogue<double>(const Geometry&, const DevT
                                                      double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_epilogue<float>(const Geometry&, const DevTables&, const float*, float*, float*,
                                                     float*, cudaStream_t);
+template cudaError_t launch_scale_planes<double>(const Geometry&, const DevTables&, const double*, double*, bool,
+                                                 cudaStream_t);
+template cudaError_t launch_scale_planes<float>(const Geometry&, const DevTables&, const float*, float*, bool,
+                                                cudaStream_t);
 template cudaError_t launch_check_finite<double>(const double*, size_t, int*, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, size_t, int*, cudaStream_t);
 

@@ -302,3 +302,24 @@ def test_bounded_wait_runs_out_and_reports_timeout(P):
     torch.cuda.synchronize()
     assert good.device_status() == 0
     assert relerr(got.cpu().numpy(), oracle.solve(g, f)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,steps,tol", [(0, 1, 1e-12), (1, 1, 2e-5), (2, 2, 1e-12)])
+def test_solve_adjoint_matches_oracle_transpose(P, prec, steps, tol):
+    """poisson_solve_adjoint = S^T (the transpose of the gauged solve) against the oracle's
+    solve_transposed, itself pinned to the dense transpose of the oracle's solve."""
+    nx, ny, nz = 48, 24, 32
+    faces = W.tanh_faces(ny, 1.9)
+    g = oracle.Grid(nx, nz, faces)
+    r = np.random.default_rng(12).standard_normal((ny, nz, nx))
+    want = oracle.solve_transposed(g, r)
+    dtype = torch.float32 if prec == P.PP_FP32 else torch.float64
+    plan = P.Plan(nx, ny, nz, faces, precision=prec, pdd_parts=4, fp64_low_modes=4, refine_steps=steps, device=DEV)
+    rt = to_dev(r, dtype)
+    got = plan.solve_adjoint(rt)
+    torch.cuda.synchronize()
+    assert relerr(got.double().cpu().numpy(), want) <= tol
+    same = rt.clone()
+    plan.solve_adjoint(same, out=same)   # in place
+    torch.cuda.synchronize()
+    assert relerr(same.double().cpu().numpy(), want) <= tol
