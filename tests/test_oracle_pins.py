@@ -297,6 +297,19 @@ def test_solve_transposed_is_the_transpose_of_solve():
     assert np.max(np.abs(ST - S.T)) <= 1e-12 * np.max(np.abs(S))
 
 
+def test_solve_transposed_equals_volume_weighted_solve():
+    """S^T r = W S(W^-1 r) with W = diag(dy_j): L_h^T = W L_h W^-1, and the rhs-mean removal and the
+    zero-weighted-mean gauge of S transpose into each other (the identity the adjoint solve of the
+    library is built on; the oracle computes S^T through the transposed systems instead)."""
+    g = _grid(12, 10, 8, stretch=1.9)
+    r = np.random.default_rng(21).standard_normal((10, 8, 12))
+    dy = g.dy[:, None, None]
+    want = oracle.solve_transposed(g, r)
+    got = dy * oracle.solve(g, r / dy)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    assert abs(want.sum()) <= 1e-12 * np.abs(want).sum()
+
+
 def test_projection_adjoint_brute_force_and_dot_product():
     nx, ny, nz = 4, 5, 4
     g = _grid(nx, ny, nz, stretch=1.4)
