@@ -91,3 +91,29 @@ def test_status_strings(native):
     assert native.status_string(0) == "ok"
     assert "invalid" in native.status_string(1)
     assert native.status_string(99) == "unknown status"
+
+
+def test_entry_points_validate_before_any_device_work(native):
+    """Null arguments and a plan without workspace are rejected synchronously (no CUDA call is
+    reached), for the solve, its adjoint and the projection."""
+    d, _ = _desc(native, precision=2)
+    h = ctypes.c_void_p()
+    L = native.lib()
+    assert L.poisson_plan_create(ctypes.byref(d), ctypes.byref(h)) == 0
+    try:
+        buf = (ctypes.c_double * 4)()
+        p = ctypes.cast(buf, ctypes.c_void_p)
+        assert L.poisson_solve_adjoint(None, p, p, None) == native.PS_EINVAL
+        assert L.poisson_solve_adjoint(h, None, p, None) == native.PS_EINVAL
+        assert L.poisson_solve_adjoint(h, p, None, None) == native.PS_EINVAL
+        assert L.poisson_solve_adjoint(h, p, p, None) == native.PS_ENOWORKSPACE
+        assert L.poisson_solve(h, p, p, None) == native.PS_ENOWORKSPACE
+        assert L.projection_step(h, p, p, p, None, 1e-3, None) == native.PS_ENOWORKSPACE
+    finally:
+        L.poisson_plan_destroy(h)
+
+
+def test_selftest_flag_is_accepted_by_the_planner(native):
+    d, _ = _desc(native, nx=512, ny=4, nz=16, faces=W.tanh_faces(4, 1.5), precision=2,
+                 flags=native.POISSON_SELFTEST_WAIT)
+    assert _create(native, d)[0] == 0
