@@ -103,7 +103,8 @@ poisson_status poisson_set_workspace(poisson_plan_t plan, void* workspace, size_
 
 /* Solve L_h p = rhs - <rhs> with zero volume-weighted mean of p (Eqs. 7-9).
  * rhs, p: device [ny][nz][nx]; FP64 for PP_FP64 and PP_FP32_REFINED, FP32 for PP_FP32.
- * rhs == p (in place) is allowed. */
+ * rhs == p (in place) is allowed for PP_FP64 and PP_FP32; PP_FP32_REFINED re-reads rhs for
+ * its residual and returns PS_EINVAL when rhs == p. */
 poisson_status poisson_solve(poisson_plan_t plan, const void* rhs, void* p, void* stream);
 
 /* The transpose of poisson_solve as a linear map of rhs (its adjoint, for gradient-based
@@ -117,21 +118,28 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* g, void* q
 /* One projection (Eqs. 4 and 7): p solves L_h p = D(u_star) / dt (made compatible), then
  * u = u_star - dt G p in place on u, v, w.  The wall faces of v are boundary values: they enter D
  * and are not modified.  p_out (device [ny][nz][nx], may be NULL) receives p.
- * Field dtype as for poisson_solve (PP_FP32_REFINED is not accepted here). */
+ * Field dtype as for poisson_solve.  PP_FP32_REFINED (FP64 fields): u, v, w are converted in
+ * place to FP32 pairs, D(u)/dt is assembled in FP64 into p_out, which is therefore REQUIRED
+ * (PS_EINVAL when NULL or aliased with u, v or w), solved by the refined solve and replaced by
+ * p; u, v, w are written back in FP64 (after a round trip through FP32 pairs, so the wall
+ * faces of v keep their values to 2^-48 relative).  With POISSON_CHECK_FINITE, u, v and w are
+ * scanned. */
 poisson_status projection_step(poisson_plan_t plan, void* u, void* v, void* w, void* p_out,
                                double dt, void* stream);
 
 /* Adjoint of the velocity map of projection_step (which does not depend on dt):
  * g <- g - D^T S^T G^T g in place, S the gauged solve.  Uses the same FFT and PDD kernels:
  * L_h^T = W L_h W^-1 with W = diag(dy_j), so the transposed solve is a forward solve of a
- * row-scaled right-hand side. */
+ * row-scaled right-hand side.  PP_FP64 and PP_FP32 plans; PP_FP32_REFINED plans return
+ * PS_EUNSUPPORTED (an FP64-accurate adjoint is served by a PP_FP64 plan). */
 poisson_status projection_step_adjoint(poisson_plan_t plan, void* gu, void* gv, void* gw,
                                        void* stream);
 
 /* End-to-end variant of projection_step on HOST buffers: copies u, v, w to the device
  * staging buffers (caller-owned device memory of the field sizes), runs projection_step,
  * copies u, v, w (and p when p_host != NULL, using p_dev) back and synchronises `stream`.
- * Host buffers should be page-locked for asynchronous copies. */
+ * PP_FP32_REFINED needs p_dev (see projection_step).  Host buffers should be page-locked for
+ * asynchronous copies. */
 poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_host,
                                     void* w_host, void* p_host, void* u_dev, void* v_dev,
                                     void* w_dev, void* p_dev, double dt, void* stream);
@@ -147,7 +155,9 @@ poisson_status projection_step_host(poisson_plan_t plan, void* u_host, void* v_h
  * wall faces of v are boundary values and are not modified.
  * ub, vb, wb: caller-owned device scratch of the sizes of u, v, w (they receive u_bar).
  * All six buffers must be distinct; dt > 0, nu >= 0, fx finite.  PP_FP64 and PP_FP32 plans
- * (PP_FP32_REFINED: PS_EUNSUPPORTED). */
+ * compute in their precision; PP_FP32_REFINED plans (FP64 fields) run both stages in
+ * double-float arithmetic on FP32 pairs (u, v, w and the scratch hold pairs in between) and
+ * return u_star in FP64.  With POISSON_CHECK_FINITE, u, v and w are scanned. */
 poisson_status momentum_predictor(poisson_plan_t plan, void* u, void* v, void* w, void* ub, void* vb,
                                   void* wb, double dt, double nu, double fx, void* stream);
 
@@ -177,12 +187,15 @@ poisson_status projection_timestep_host(poisson_plan_t plan, void* u_host, void*
  * created by poisson_plan_create; poisson_set_workspace is not needed).  The workspace is a
  * fixed device array of POISSON_STATIC_WS_MAX_BYTES inside the library, held by every GPU
  * that loads the library until the process exits; plans whose poisson_workspace_size exceeds
- * it are rejected with PS_EUNSUPPORTED.  No cudaMalloc, cudaFree or other allocator is
- * called.  The first call on each device looks up the array's device address (with that
- * device current), so make that first call before any stream capture.  Every call reloads
- * the plan's tables into the array and clears its status word; all calls share the one array
- * per device, so calls that overlap on the GPU (different streams, threads or plans) race:
- * serialise them. */
+ * it are rejected with PS_EUNSUPPORTED, batched plans with PS_EINVAL.  No cudaMalloc, cudaFree
+ * or other allocator is called.  The first call on each device looks up the array's device
+ * address (with that device current; the lookup is serialised by a lock, so concurrent first
+ * calls are safe), so make that first call before any stream capture.  The address is kept
+ * for the life of the process: after cudaDeviceReset on a device, do not call this entry point
+ * on that device again.  Every call reloads the plan's tables into the array from ordinary
+ * (pageable) host memory, so the call returns only once `stream` has reached that copy, and
+ * clears the array's status word; all calls share the one array per device, so calls that
+ * overlap on the GPU (different streams, threads or plans) race: serialise them. */
 poisson_status poisson_solve_static_ws(poisson_plan_t plan, const void* rhs, void* p, void* stream);
 
 /* Batched form: `count` independent solves of possibly different sizes and precisions
@@ -207,6 +220,20 @@ poisson_status poisson_solve_batched(poisson_plan_t plan, const void* const* rhs
  * (set-up time, not the solve path) and synchronises `stream`. */
 poisson_status poisson_autotune(const poisson_desc* desc, void* stream, int* pdd_parts, unsigned* flags,
                                 float* ms);
+
+/* Tuning of the FP32 spectral middle (Sec. 3.2 steps (4)-(6): forward z-transform, wall-normal
+ * systems, inverse z-transform).  slab_cols > 0 runs the three passes one slab of slab_cols kx
+ * columns at a time, so a slab (ny * nz * slab_cols complex values) stays in L2 between the
+ * passes; streams = 2 alternates the slabs between the caller's stream and a second stream owned
+ * by the plan (forked and joined with events, so the call stays stream-ordered on the caller's
+ * stream).  slab_cols = 0 restores one pass over the whole spectrum.  Needs a PP_FP32 or
+ * PP_FP32_REFINED plan whose blocks use the warp-scan PDD kernel (pdd_parts a power of two
+ * <= 32 with ny/pdd_parts in {1,2,3,4,6,8,12,16,24}) and the specialised z-transform (nz in
+ * {16,...,1024} of the form 2^a 3^b, no POISSON_GENERIC_FFT), slab_cols a multiple of the z tile
+ * and of 256/pdd_parts and larger than fp64_low_modes (PS_EUNSUPPORTED otherwise).  Call with
+ * the plan's device current (the second stream is created then); results are identical to the
+ * whole-spectrum order. */
+poisson_status poisson_plan_set_chain(poisson_plan_t plan, int slab_cols, int streams);
 
 /* Synchronise `stream` and read the device status word (PS_OK, PS_ENONFINITE, ...),
  * then clear it. */

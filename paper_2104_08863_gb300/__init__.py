@@ -96,11 +96,16 @@ class Plan:
         return out
 
     def project(self, u, v, w, dt: float, p_out=None, stream=None):
-        """In-place projection of (u, v, w); returns p_out (or None)."""
+        """In-place projection of (u, v, w); returns p_out (or None).
+
+        PP_FP32_REFINED plans need a pressure buffer (it carries the FP64 right-hand side during
+        the solve): one is allocated when p_out is None, and returned."""
         self._check(u, self.cell_shape, "u")
         self._check(v, self.v_shape, "v")
         self._check(w, self.cell_shape, "w")
         pp = 0
+        if p_out is None and self.precision == PP_FP32_REFINED:
+            p_out = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
         if p_out is not None:
             self._check(p_out, self.cell_shape, "p_out")
             pp = _ptr(p_out)
@@ -166,6 +171,12 @@ class Plan:
             self._h, _ptr(u_h), _ptr(v_h), _ptr(w_h), _ptr(p_h) if p_h is not None else 0,
             _ptr(u_d), _ptr(v_d), _ptr(w_d), _ptr(p_d) if p_d is not None else 0, float(dt), _stream(stream)),
             "projection_step_host")
+
+    def set_chain(self, slab_cols: int, streams: int = 1):
+        """Run the FP32 z-transform / wall-normal / inverse z-transform passes in kx slabs of
+        slab_cols columns (0: whole spectrum) over 1 or 2 streams (poisson_plan_set_chain)."""
+        with torch.cuda.device(self.device):
+            check(_native.lib().poisson_plan_set_chain(self._h, int(slab_cols), int(streams)), "poisson_plan_set_chain")
 
     def device_status(self, stream=None) -> int:
         return int(_native.lib().poisson_device_status(self._h, _stream(stream)))

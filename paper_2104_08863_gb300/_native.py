@@ -26,7 +26,8 @@ EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
     "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
     "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
-    "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
+    "projection_timestep", "projection_timestep_host", "poisson_plan_set_chain", "poisson_device_status",
+    "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
 
@@ -75,6 +76,7 @@ def lib() -> ctypes.CDLL:
     L.momentum_predictor.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
     L.projection_timestep.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
     L.projection_timestep_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
+    L.poisson_plan_set_chain.argtypes = [vp, i, i]
     L.poisson_device_status.argtypes = [vp, vp]
     L.poisson_last_launch_count.argtypes = [vp]
     L.poisson_last_launch_count.restype = i
@@ -86,7 +88,8 @@ def lib() -> ctypes.CDLL:
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
                  "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
                  "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
-                 "projection_timestep", "projection_timestep_host", "poisson_device_status", "poisson_plan_destroy"):
+                 "projection_timestep", "projection_timestep_host", "poisson_plan_set_chain", "poisson_device_status",
+                 "poisson_plan_destroy"):
         getattr(L, name).restype = i
     _LIB = L
     return L

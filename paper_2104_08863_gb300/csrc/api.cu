@@ -396,8 +396,16 @@ void timer_end(Exec& ex, const char* name) {
     if (_s != PS_OK) return _s;          \
   } while (0)
 
-// Spectral middle of a solve on the z-transformed spectral buffer: wall-normal systems and the
-// (0, 0) mode.
+// A launch inside a region that is timed as a whole (no event pair of its own).
+#define PP_TRY_Q(expr)                                    \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    ++ex.pl->launches;                                    \
+    if (_e != cudaSuccess) return PS_ECUDA;               \
+  } while (0)
+
+// Spectral middle of a solve on the x-transformed spectral buffer (Sec. 3.2 steps (4)-(6)):
+// forward z-transform, wall-normal systems, the (0, 0) mode, inverse z-transform.
 template <typename T>
 poisson_status spectral_mid(Exec& ex, cplx<T>* spec, GaugeMode gauge);
 
@@ -406,8 +414,48 @@ poisson_status spectral_mid<double>(Exec& ex, cplx<double>* spec, GaugeMode gaug
   const poisson_plan_s* pl = ex.pl;
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
+  PP_TRY_N("fft_z_fwd", launch_fft_z<double>(g, ex.dt, pl->fz, -1, spec, st));
   PP_TRY_N("tridiag_pdd", launch_tridiag_factored(g, ex.dt, pl->parts, pl->tridiag == PT_PDD_TRUNCATED, spec, st));
   PP_TRY_N("mode00", launch_mode00<double>(g, ex.dt, gauge, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<double>(g, ex.dt, pl->fz, +1, spec, st));
+  return PS_OK;
+}
+
+// The FP32 spectral middle in kx slabs (poisson_plan_set_chain): for each slab of slab_cols
+// columns the forward z-transform, the wall-normal solves and the inverse z-transform run back
+// to back, so the slab (ny nz slab_cols complex values) is still in L2 when the next pass reads
+// it and the spectrum crosses HBM once in each direction for the three passes.  Slabs are
+// independent (disjoint columns); with two streams, odd slabs run on the plan's second stream
+// (forked from and joined back into the caller's stream by events), which fills the tail of one
+// slab's launch with the next slab's work.  The low modes and the (0, 0) mode lie in slab 0.
+poisson_status spectral_chain_f32(Exec& ex, cplx<float>* spec, GaugeMode gauge) {
+  const poisson_plan_s* pl = ex.pl;
+  const Geometry& g = pl->g;
+  cudaStream_t st = ex.st;
+  const int sw = pl->slab_cols;
+  const bool two = pl->chain_streams > 1 && pl->chain_st != nullptr;
+  cplx<double>* scr = (cplx<double>*)(ex.ws + pl->off_scratch);
+  const bool timed = timer_begin(ex);
+  if (two) {
+    if (cudaEventRecord(pl->chain_ev[0], st) != cudaSuccess) return PS_ECUDA;
+    if (cudaStreamWaitEvent(pl->chain_st, pl->chain_ev[0], 0) != cudaSuccess) return PS_ECUDA;
+  }
+  for (int k = 0, lo = 0; lo < g.ncols; ++k, lo += sw) {
+    const int hi = lo + sw < g.ncols ? lo + sw : g.ncols;
+    cudaStream_t s = (two && (k & 1)) ? pl->chain_st : st;
+    PP_TRY_Q(launch_fft_z_fast<float>(g, ex.dt.f, -1, spec, s, lo, hi));
+    PP_TRY_Q(launch_tridiag_reg_f32(g, ex.dt, pl->parts, pl->low, spec, s, lo, hi));
+    if (lo == 0) {
+      if (pl->low >= 0) PP_TRY_Q(launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, s));
+      PP_TRY_Q(launch_mode00<float>(g, ex.dt, gauge, spec, s));
+    }
+    PP_TRY_Q(launch_fft_z_fast<float>(g, ex.dt.f, +1, spec, s, lo, hi));
+  }
+  if (two) {
+    if (cudaEventRecord(pl->chain_ev[1], pl->chain_st) != cudaSuccess) return PS_ECUDA;
+    if (cudaStreamWaitEvent(st, pl->chain_ev[1], 0) != cudaSuccess) return PS_ECUDA;
+  }
+  if (timed) timer_end(ex, "z_pdd_z_chain");
   return PS_OK;
 }
 
@@ -416,6 +464,8 @@ poisson_status spectral_mid<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge)
   const poisson_plan_s* pl = ex.pl;
   const Geometry& g = pl->g;
   cudaStream_t st = ex.st;
+  if (pl->slab_cols > 0) return spectral_chain_f32(ex, spec, gauge);
+  PP_TRY_N("fft_z_fwd", launch_fft_z<float>(g, ex.dt, pl->fz, -1, spec, st));
   if (pl->has_tri)
     PP_TRY_N("tridiag_pdd", launch_tridiag_factored_f32(g, ex.dt, pl->parts, pl->low, pl->tridiag == PT_PDD_TRUNCATED,
                                                         spec, st));
@@ -425,28 +475,29 @@ poisson_status spectral_mid<float>(Exec& ex, cplx<float>* spec, GaugeMode gauge)
     PP_TRY_N("tridiag_low64", launch_tridiag_low64(g, ex.dt, pl->parts, pl->low, spec, scr, st));
   }
   PP_TRY_N("mode00", launch_mode00<float>(g, ex.dt, gauge, spec, st));
+  PP_TRY_N("fft_z_inv", launch_fft_z<float>(g, ex.dt, pl->fz, +1, spec, st));
   return PS_OK;
 }
 
-// Forward x- and z-transforms of the right-hand side of `mode`, then the spectral middle.
+// Forward x-transform of the right-hand side of `mode`, then the spectral middle (which ends
+// with the inverse z-transform).
 template <typename T, typename TI>
 poisson_status forward_and_core(Exec& ex, FwdMode mode, const FwdArgs& args, GaugeMode gauge) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   cudaStream_t st = ex.st;
   static const char* const fwd_names[] = {"fwd_x", "fwd_x_div", "fwd_x_resid", "fwd_x_gradt"};
   PP_TRY_N(fwd_names[mode], (launch_fwd_x<T, TI>(ex.pl->g, ex.dt, ex.pl->fm, mode, args, spec, st)));
-  PP_TRY_N("fft_z_fwd", launch_fft_z<T>(ex.pl->g, ex.dt, ex.pl->fz, -1, spec, st));
   return spectral_mid<T>(ex, spec, gauge);
 }
 
-// Inverse z- and x-transforms of the spectral buffer into `out` with the epilogue `mode`.
+// Inverse x-transform of the spectral buffer (already inverse z-transformed) into `out` with
+// the epilogue `mode`.
 template <typename T, typename TO>
 poisson_status inverse_x(Exec& ex, InvMode mode, TO* out, bool accumulate, PairArgs pair = PairArgs{nullptr, nullptr}) {
   cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec);
   const double scale = 1.0 / ((double)ex.pl->g.nx * (double)ex.pl->g.nz);
   cudaStream_t st = ex.st;
   static const char* const inv_names[] = {"inv_x", "inv_x_accum", "inv_x_final"};
-  PP_TRY_N("fft_z_inv", launch_fft_z<T>(ex.pl->g, ex.dt, ex.pl->fz, +1, spec, st));
   PP_TRY_N(inv_names[mode], (launch_inv_x<T, TO>(ex.pl->g, ex.dt, ex.pl->fm, mode, spec, out, scale, accumulate, st,
                                                  pair)));
   return PS_OK;
@@ -466,6 +517,14 @@ poisson_status check_finite(Exec& ex, const void* x, size_t n) {
   cudaStream_t st = ex.st;
   PP_TRY_N("check_finite", launch_check_finite<T>((const T*)x, n, ex.dt.status, st));
   return PS_OK;
+}
+
+// POISSON_CHECK_FINITE on a velocity triple (u, w cell-sized, v with its ny+1 face planes).
+template <typename T>
+poisson_status check_finite_uvw(Exec& ex, const void* u, const void* v, const void* w) {
+  PP_RET(check_finite<T>(ex, u, cell_count(ex.pl)));
+  PP_RET(check_finite<T>(ex, v, vface_count(ex.pl)));
+  return check_finite<T>(ex, w, cell_count(ex.pl));
 }
 
 // The solve of poisson_solve on any workspace (caller-owned or the library's static one).
@@ -534,17 +593,38 @@ poisson_status projection_impl(Exec& ex, void* u, void* v, void* w, void* p_out,
   args.in_scale = 1.0 / dt;
   if (pl->precision == PP_FP64) {
     double* p = p_out ? (double*)p_out : (double*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+    PP_RET(check_finite_uvw<double>(ex, u, v, w));
     PP_RET((forward_and_core<double, double>(ex, FWD_DIV, args, GAUGE_ZERO)));
     PP_RET((inverse_x<double, double>(ex, INV_STORE, p, false)));
     PP_TRY_N("gradient", launch_gradient<double>(pl->g, ex.dt, p, (double*)u, (double*)v, (double*)w, dt, st));
   } else {
     float* p = p_out ? (float*)p_out : (float*)(pl->ws + pl->off_pbuf);
-    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
+    PP_RET(check_finite_uvw<float>(ex, u, v, w));
     PP_RET((forward_and_core<float, float>(ex, FWD_DIV, args, GAUGE_ZERO)));
     PP_RET((inverse_x<float, float>(ex, INV_STORE, p, false)));
     PP_TRY_N("gradient", launch_gradient<float>(pl->g, ex.dt, p, (float*)u, (float*)v, (float*)w, dt, st));
   }
+  return PS_OK;
+}
+
+// The projection of PP_FP32_REFINED plans (Eqs. 4 and 7) without per-point FP64 arithmetic:
+// u, v, w converted in place to FP32 pairs, f = D(u)/dt assembled in FP64 into p_out (the
+// solve's right-hand side), the refined solve into the workspace's pressure pair, then
+// u = u - dt G p written in FP64 over the pairs and p (FP64) over f in p_out.
+poisson_status projection_pairs(Exec& ex, void* u, void* v, void* w, void* p_out, double dt) {
+  const poisson_plan_s* pl = ex.pl;
+  PP_RET(check_finite_uvw<double>(ex, u, v, w));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)u, cell_count(pl), ex.st));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)v, vface_count(pl), ex.st));
+  PP_TRY_N("to_pairs", launch_to_pairs((double*)w, cell_count(pl), ex.st));
+  double* f = (double*)p_out;
+  PP_TRY_N("divergence_df", launch_divergence_df(pl->g, ex.dt, (const float2*)u, (const float2*)v,
+                                                 (const float2*)w, dt, f, ex.st));
+  PP_RET(solve_impl(ex, f, nullptr, true));
+  const float* hi = (const float*)(ex.ws + pl->off_pbuf);
+  const float* lo = (const float*)(ex.ws + pl->off_pbuf2);
+  PP_TRY_N("gradient_pairs", launch_gradient_pairs(pl->g, ex.dt, hi, lo, (double*)u, (double*)v, (double*)w,
+                                                   (double*)p_out, dt, ex.st));
   return PS_OK;
 }
 
@@ -569,7 +649,7 @@ poisson_status check_timestep_args(const poisson_plan_s* pl, const void* u, cons
 poisson_status predictor_pairs(Exec& ex, void* u, void* v, void* w, void* ub, void* vb, void* wb, double dt,
                                double nu, double fx) {
   const poisson_plan_s* pl = ex.pl;
-  PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+  PP_RET(check_finite_uvw<double>(ex, u, v, w));
   PP_TRY_N("to_pairs", launch_to_pairs((double*)u, cell_count(pl), ex.st));
   PP_TRY_N("to_pairs", launch_to_pairs((double*)v, vface_count(pl), ex.st));
   PP_TRY_N("to_pairs", launch_to_pairs((double*)w, cell_count(pl), ex.st));
@@ -588,7 +668,7 @@ poisson_status predictor_impl(Exec& ex, void* u, void* v, void* w, void* ub, voi
                               double nu, double fx) {
   const poisson_plan_s* pl = ex.pl;
   if (pl->precision == PP_FP64) {
-    PP_RET(check_finite<double>(ex, u, cell_count(pl)));
+    PP_RET(check_finite_uvw<double>(ex, u, v, w));
     MomArgs<double> s1{(const double*)u, (const double*)v, (const double*)w, nullptr, nullptr, nullptr,
                        (double*)ub, (double*)vb, (double*)wb, 0.0, 1.0, dt, nu, fx};
     PP_TRY_N("momentum_1", launch_momentum<double>(pl->g, ex.dt, s1, ex.st));
@@ -597,7 +677,7 @@ poisson_status predictor_impl(Exec& ex, void* u, void* v, void* w, void* ub, voi
                        0.5, 0.5, 0.5 * dt, nu, fx};
     PP_TRY_N("momentum_2", launch_momentum<double>(pl->g, ex.dt, s2, ex.st));
   } else {
-    PP_RET(check_finite<float>(ex, u, cell_count(pl)));
+    PP_RET(check_finite_uvw<float>(ex, u, v, w));
     MomArgs<float> s1{(const float*)u, (const float*)v, (const float*)w, nullptr, nullptr, nullptr,
                       (float*)ub, (float*)vb, (float*)wb, 0.0, 1.0, dt, nu, fx};
     PP_TRY_N("momentum_1", launch_momentum<float>(pl->g, ex.dt, s1, ex.st));
@@ -672,10 +752,19 @@ poisson_status projection_step(poisson_plan_t pl, void* u, void* v, void* w, voi
   if (!pl->ws) return PS_ENOWORKSPACE;
   if (!(dt > 0.0) || !isfinite(dt)) return PS_EINVAL;
   if (!aligned16(u) || !aligned16(v) || !aligned16(w) || (p_out && !aligned16(p_out))) return PS_EINVAL;
-  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  if (!pl->children.empty()) return PS_EINVAL;
+  if (pl->precision == PP_FP32_REFINED) {
+    // p_out carries the FP64 right-hand side during the solve, so it is required here
+    if (!p_out) return PS_EINVAL;
+    const void* all[4] = {u, v, w, p_out};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < a; ++b)
+        if (all[a] == all[b]) return PS_EINVAL;
+  }
   pl->launches = 0;
   pl->nev = 0;
   Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  if (pl->precision == PP_FP32_REFINED) return projection_pairs(ex, u, v, w, p_out, dt);
   return projection_impl(ex, u, v, w, p_out, dt);
 }
 
@@ -749,14 +838,15 @@ poisson_status projection_step_host(poisson_plan_t pl, void* u_h, void* v_h, voi
                                     void* v_d, void* w_d, void* p_d, double dt, void* stream) {
   if (!pl || !u_h || !v_h || !w_h || !u_d || !v_d || !w_d) return PS_EINVAL;
   if (p_h && !p_d) return PS_EINVAL;
-  if (pl->precision == PP_FP32_REFINED) return PS_EUNSUPPORTED;
+  if (pl->precision == PP_FP32_REFINED && !p_d) return PS_EINVAL;   // the solve's right-hand side
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t es = pl->precision == PP_FP64 ? 8 : 4;
+  const size_t es = pl->precision == PP_FP32 ? 4 : 8;
   const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
   if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-  PP_RET(projection_step(pl, u_d, v_d, w_d, p_h ? p_d : nullptr, dt, stream));
+  void* pd = (p_h || pl->precision == PP_FP32_REFINED) ? p_d : nullptr;
+  PP_RET(projection_step(pl, u_d, v_d, w_d, pd, dt, stream));
   if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
@@ -783,6 +873,30 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (p_h && cudaMemcpyAsync(p_h, p_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  return PS_OK;
+}
+
+poisson_status poisson_plan_set_chain(poisson_plan_t pl, int slab_cols, int streams) {
+  if (!pl || !pl->children.empty() || slab_cols < 0 || streams < 1 || streams > 2) return PS_EINVAL;
+  if (slab_cols == 0) {
+    pl->slab_cols = 0;
+    pl->chain_streams = 1;
+    return PS_OK;
+  }
+  const Geometry& g = pl->g;
+  const int wz = pp::fft_z_fast_tile<float>(g);
+  const bool path_ok = pl->precision != PP_FP64 && !pl->has_tri && pp::scan_tridiag_ok(g.ny, pl->parts) &&
+                       !g.generic_fft && wz > 0;
+  if (!path_ok) return PS_EUNSUPPORTED;
+  const int step = wz > pp::reg_systems_per_cta(pl->parts) ? wz : pp::reg_systems_per_cta(pl->parts);
+  if (slab_cols % step || slab_cols <= pl->low) return PS_EUNSUPPORTED;
+  if (streams == 2 && !pl->chain_st) {
+    if (cudaStreamCreateWithFlags(&pl->chain_st, cudaStreamNonBlocking) != cudaSuccess) return PS_ECUDA;
+    for (cudaEvent_t& e : pl->chain_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PS_ECUDA;
+  }
+  pl->slab_cols = slab_cols;
+  pl->chain_streams = streams;
   return PS_OK;
 }
 
@@ -817,6 +931,9 @@ int poisson_stage_times(poisson_plan_t pl, float* ms, const char** names, int ma
 poisson_status poisson_plan_destroy(poisson_plan_t pl) {
   if (pl) {
     for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+    if (pl->chain_st) cudaStreamDestroy(pl->chain_st);
+    for (cudaEvent_t e : pl->chain_ev)
+      if (e) cudaEventDestroy(e);
     pp::destroy_batch(pl);
   }
   delete pl;

@@ -118,9 +118,13 @@ cudaError_t launch_inv_x_fast_fd(const Geometry& g, const DevTables& tb, InvMode
                                  double* out, double scale, bool accumulate, cudaStream_t st, PairArgs pair);
 
 // Specialised z-transform for Nz in {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
-// returns cudaErrorNotSupported for other lengths.
+// returns cudaErrorNotSupported for other lengths.  [kx_lo, kx_hi): the kx columns transformed
+// (kx_hi < 0: all; kx_lo a multiple of fft_z_fast_tile).
 template <typename T>
-cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st);
+cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st,
+                              int kx_lo = 0, int kx_hi = -1);
+template <typename T>
+int fft_z_fast_tile(const Geometry& g);
 
 template <typename TD, typename TC>
 cudaError_t launch_tridiag(const Geometry& g, const DevTables& tb, int parts, int low_modes, bool low_list,
@@ -150,8 +154,12 @@ inline bool reg_tridiag_ok(int ny, int P) {
   return m == 1 || m == 2 || m == 3 || m == 4 || m == 6 || m == 8 || m == 12 || m == 16 || m == 24;
 }
 inline int reg_systems_per_cta(int P) { return P >= 256 ? 1 : 256 / P; }
+// [kx_lo, kx_hi): the kx columns solved (kx_hi < 0: all); a partial range is supported by the
+// warp-scan variant only (P a power of two <= 32), with kx_lo a multiple of
+// reg_systems_per_cta(P), and is refused (cudaErrorNotSupported) otherwise.
 cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
-                                   cplx<float>* spec, cudaStream_t st);
+                                   cplx<float>* spec, cudaStream_t st, int kx_lo = 0, int kx_hi = -1);
+inline bool scan_tridiag_ok(int ny, int P) { return reg_tridiag_ok(ny, P) && P <= 32 && (P & (P - 1)) == 0; }
 // Bytes of the reduced-system table of the register kernel, and its FP64 set-up (once per plan).
 size_t reduced_table_bytes(const Geometry& g, int parts);
 cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, bool trunc, float* tab,
@@ -235,6 +243,12 @@ struct poisson_plan_s {
   unsigned char* ws;
   pp::DevTables dt;
   int launches;
+  // kx-slab chain of the FP32 spectral middle (poisson_plan_set_chain): slab width in columns
+  // (0: one pass over the whole spectrum), streams (1 or 2), the second stream and its events
+  int slab_cols = 0;
+  int chain_streams = 1;
+  cudaStream_t chain_st = nullptr;
+  cudaEvent_t chain_ev[2] = {nullptr, nullptr};
   // POISSON_TIMING: one event pair around every launch of the last call
   std::vector<cudaEvent_t> ev;
   std::vector<const char*> ev_names;

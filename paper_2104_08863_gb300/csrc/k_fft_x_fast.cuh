@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
         const ResidLine R = resid_line(g, args, tt, tb, line, mh, ml);
 #pragma unroll
         for (int n = threadIdx.x; n < M; n += THREADS) {
-          const float2 r = resid_pair_line(R, n);
+          const float2 r = resid_pair_line2(R, n);
           buf[padi<T>(t * M + n)] = mk<T>(r.x, r.y);
         }
       } else {

@@ -3,11 +3,90 @@
 // coalesced row segments of W complex values, transformed in place in (padded) shared memory
 // by the compile-time Stockham engine, and stored back.  W and the thread count are chosen so
 // that each thread stages 16 (FP32) or 8 (FP64) complex values per stage, which keeps two
-// CTAs resident per SM so that one CTA's loads overlap the other's arithmetic.
+// CTAs resident per SM so that one CTA's loads overlap the other's arithmetic.  A launch may
+// cover only the kx columns [kx_lo, kx_hi) (one slab of the spectrum; kx_lo a multiple of W).
+#include "fft_reg.cuh"
 #include "fft_static.cuh"
 #include "internal.h"
 
 namespace pp {
+
+// ---- two-pass register z-transform (FP32) ------------------------------------------------------
+// Nz = N1 x N2 (N1 >= N2, both <= 32).  A CTA owns W adjacent kx columns of one y-plane.  Pass 1:
+// thread (c, n1) loads the N2 values x[n1 + N1 n2] of column c straight from global memory into
+// registers, takes their N2-point DFT in registers, multiplies output k2 by W_Nz^{n1 k2} and writes
+// it to shared memory at [k2][n1][c].  Pass 2: thread (c, k2) reads the N1 values of its k2, takes
+// their N1-point DFT (output k1 is X[k2 + N2 k1]) and stores to global memory.  One shared-memory
+// round trip per element (the Stockham kernel makes one per stage plus two), and each thread's
+// global loads are all issued before any arithmetic.  The k2 blocks of shared memory are padded so
+// that their byte stride is 64 mod 128: the pass-2 reads of a warp (four k2 blocks of W columns)
+// then fall on alternating bank halves.
+template <typename T, int NZ> struct ZReg {
+  static constexpr int N1 = split_n1(NZ), N2 = NZ / N1;
+  static constexpr int WMIN = sizeof(T) == 4 ? 8 : 4;   // 64-byte row segments
+  static constexpr int W0 = 256 / N1;
+  static constexpr int W1 = W0 >= 32 ? 32 : (W0 >= 16 ? 16 : 8);   // a power of two: aligned row segments
+  static constexpr int W = W1 < WMIN ? WMIN : W1;
+  static constexpr int THREADS = W * N1;
+  static constexpr int CB = (int)sizeof(cplx<T>);
+  static constexpr int B0 = N1 * W;
+  static constexpr int B = B0 + (((64 - (B0 * CB) % 128) + 128) % 128) / CB;   // B * CB == 64 (mod 128)
+  static constexpr int SMEM = N2 * B * CB;
+  static_assert((B * CB) % 128 == 64, "pad");
+  static_assert(N1 <= 32 && N2 <= 32 && N1 * N2 == NZ, "split");
+};
+
+template <typename T, int NZ, int SIGN>
+__global__ void __launch_bounds__(ZReg<T, NZ>::THREADS, 2) k_fft_z_reg(Geometry g, Tables<T> tt,
+                                                                      cplx<T>* __restrict__ spec, int kx_lo,
+                                                                      int kx_hi) {
+  using C = ZReg<T, NZ>;
+  constexpr int N1 = C::N1, N2 = C::N2, W = C::W, B = C::B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int j = blockIdx.y;
+  const int kx0 = kx_lo + blockIdx.x * W;
+  cplx<T>* plane = spec + (size_t)j * NZ * g.pitch + kx0;
+  const int ncol = min(W, kx_hi - kx0);
+  const int c = threadIdx.x % W, q = threadIdx.x / W;
+  const bool cok = c < ncol;
+  {
+    const int n1 = q;   // < N1
+    cplx<T> v[N2];
+    const cplx<T>* src = plane + (size_t)n1 * g.pitch + c;
+    const size_t step = (size_t)N1 * g.pitch;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = cok ? ld_c(src + n2 * step) : mk<T>(T(0), T(0));
+    reg_dft<T, N2, SIGN>(v);
+    static_for<0, N2>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int k2 = reg_freq(N2, s);
+      cplx<T> x = v[s];
+      if constexpr (k2 != 0) {
+        const cplx<T> w = ldg_c(tt.tw_z + n1 * k2);
+        x = SIGN < 0 ? cmul(x, w) : cmulc(x, w);
+      }
+      buf[k2 * B + n1 * W + c] = x;
+    });
+  }
+  __syncthreads();
+  if (q < N2) {
+    const int k2 = q;
+    cplx<T> u[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = buf[k2 * B + n1 * W + c];
+    reg_dft<T, N1, SIGN>(u);
+    if (cok) {
+      cplx<T>* dst = plane + (size_t)k2 * g.pitch + c;
+      const size_t step = (size_t)N2 * g.pitch;
+      static_for<0, N1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        constexpr int k1 = reg_freq(N1, s);
+        st_c(dst + k1 * step, u[s]);
+      });
+    }
+  }
+}
 
 template <typename T, int NZ> struct ZTile {
   static constexpr int E = sizeof(T) == 4 ? 16 : 8;               // complex values per thread
@@ -22,15 +101,16 @@ template <typename T, int NZ> struct ZTile {
 
 template <typename T, int NZ, int SIGN>
 __global__ void __launch_bounds__(ZTile<T, NZ>::THREADS, ZTile<T, NZ>::MINB) k_fft_z_fast(Geometry g, Tables<T> tt,
-                                                                       cplx<T>* __restrict__ spec) {
+                                                                       cplx<T>* __restrict__ spec, int kx_lo,
+                                                                       int kx_hi) {
   using C = ZTile<T, NZ>;
   constexpr int W = C::W, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int j = blockIdx.y;
-  const int kx0 = blockIdx.x * W;
+  const int kx0 = kx_lo + blockIdx.x * W;
   cplx<T>* plane = spec + (size_t)j * NZ * g.pitch + kx0;
-  const int ncol = min(W, g.ncols - kx0);
+  const int ncol = min(W, kx_hi - kx0);
   {
     // every load of the thread is issued before its first shared-memory store
     constexpr int PER = (NZ * W + THREADS - 1) / THREADS;
@@ -62,45 +142,78 @@ static cudaError_t set_smem_once(K kernel, int smem) {
 }
 
 template <typename T, int NZ>
-static cudaError_t launch_z(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st) {
+static cudaError_t launch_z_reg(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st,
+                                int kx_lo, int kx_hi) {
+  using C = ZReg<T, NZ>;
+  if (kx_lo % C::W || kx_lo < 0 || kx_hi > g.ncols || kx_hi <= kx_lo) return cudaErrorInvalidValue;
+  const dim3 grid((kx_hi - kx_lo + C::W - 1) / C::W, g.ny);
+  cudaError_t e;
+  if (sign < 0) {
+    auto k = k_fft_z_reg<T, NZ, -1>;
+    if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, kx_lo, kx_hi);
+  } else {
+    auto k = k_fft_z_reg<T, NZ, 1>;
+    if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, kx_lo, kx_hi);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int NZ>
+static cudaError_t launch_z(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st,
+                            int kx_lo, int kx_hi) {
+  if constexpr (sizeof(T) == 4) return launch_z_reg<T, NZ>(g, tt, sign, spec, st, kx_lo, kx_hi);
   using C = ZTile<T, NZ>;
-  const dim3 grid((g.ncols + C::W - 1) / C::W, g.ny);
+  if (kx_lo % C::W || kx_lo < 0 || kx_hi > g.ncols || kx_hi <= kx_lo) return cudaErrorInvalidValue;
+  const dim3 grid((kx_hi - kx_lo + C::W - 1) / C::W, g.ny);
   cudaError_t e;
   if (sign < 0) {
     auto k = k_fft_z_fast<T, NZ, -1>;
     if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
-    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, kx_lo, kx_hi);
   } else {
     auto k = k_fft_z_fast<T, NZ, 1>;
     if ((e = set_smem_once(k, C::SMEM)) != cudaSuccess) return e;
-    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec);
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tt, spec, kx_lo, kx_hi);
   }
   return cudaGetLastError();
 }
 
 // Returns cudaErrorNotSupported when Nz has no specialisation (the caller then uses the
-// generic kernel).
+// generic kernel).  kx_hi < 0 means all columns.
 template <typename T>
-cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st) {
+cudaError_t launch_fft_z_fast(const Geometry& g, const Tables<T>& tt, int sign, cplx<T>* spec, cudaStream_t st,
+                              int kx_lo, int kx_hi) {
+  if (kx_hi < 0) kx_hi = g.ncols;
   switch (g.nz) {
-    case 16: return launch_z<T, 16>(g, tt, sign, spec, st);
-    case 32: return launch_z<T, 32>(g, tt, sign, spec, st);
-    case 48: return launch_z<T, 48>(g, tt, sign, spec, st);
-    case 64: return launch_z<T, 64>(g, tt, sign, spec, st);
-    case 96: return launch_z<T, 96>(g, tt, sign, spec, st);
-    case 128: return launch_z<T, 128>(g, tt, sign, spec, st);
-    case 192: return launch_z<T, 192>(g, tt, sign, spec, st);
-    case 256: return launch_z<T, 256>(g, tt, sign, spec, st);
-    case 384: return launch_z<T, 384>(g, tt, sign, spec, st);
-    case 512: return launch_z<T, 512>(g, tt, sign, spec, st);
-    case 768: return launch_z<T, 768>(g, tt, sign, spec, st);
-    case 1024: return launch_z<T, 1024>(g, tt, sign, spec, st);
+#define PP_Z_CASE(NZ) \
+    case NZ: return launch_z<T, NZ>(g, tt, sign, spec, st, kx_lo, kx_hi);
+    PP_Z_CASE(16) PP_Z_CASE(32) PP_Z_CASE(48) PP_Z_CASE(64) PP_Z_CASE(96) PP_Z_CASE(128) PP_Z_CASE(192)
+    PP_Z_CASE(256) PP_Z_CASE(384) PP_Z_CASE(512) PP_Z_CASE(768) PP_Z_CASE(1024)
+#undef PP_Z_CASE
     default: return cudaErrorNotSupported;
   }
 }
 
-template cudaError_t launch_fft_z_fast<float>(const Geometry&, const Tables<float>&, int, cplx<float>*, cudaStream_t);
+// Column width of the specialised z tile for this Nz (0 when Nz has no specialisation).
+template <typename T>
+int fft_z_fast_tile(const Geometry& g) {
+  switch (g.nz) {
+#define PP_ZW_CASE(NZ) \
+    case NZ: return sizeof(T) == 4 ? ZReg<T, NZ>::W : ZTile<T, NZ>::W;
+    PP_ZW_CASE(16) PP_ZW_CASE(32) PP_ZW_CASE(48) PP_ZW_CASE(64) PP_ZW_CASE(96) PP_ZW_CASE(128) PP_ZW_CASE(192)
+    PP_ZW_CASE(256) PP_ZW_CASE(384) PP_ZW_CASE(512) PP_ZW_CASE(768) PP_ZW_CASE(1024)
+#undef PP_ZW_CASE
+    default: return 0;
+  }
+}
+
+template cudaError_t launch_fft_z_fast<float>(const Geometry&, const Tables<float>&, int, cplx<float>*, cudaStream_t,
+                                              int, int);
 template cudaError_t launch_fft_z_fast<double>(const Geometry&, const Tables<double>&, int, cplx<double>*,
-                                               cudaStream_t);
+                                               cudaStream_t, int, int);
+template int fft_z_fast_tile<float>(const Geometry&);
+template int fft_z_fast_tile<double>(const Geometry&);
 
 }  // namespace pp

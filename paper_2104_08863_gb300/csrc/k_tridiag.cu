@@ -666,7 +666,7 @@ template <int M>
 __global__ void __launch_bounds__(256, 2) k_tridiag_scan(Geometry g, int P, int S, int low, const float* __restrict__ a,
                                                          const float* __restrict__ c, const double* __restrict__ lamx,
                                                          const double* __restrict__ lamz, const float* __restrict__ rtab,
-                                                         cplx<float>* __restrict__ spec) {
+                                                         cplx<float>* __restrict__ spec, int kx_lo, int kx_hi) {
   extern __shared__ __align__(16) float2 tile[];   // [b][i][s] with block stride BS, then a and c
   const int NT = P * S;
   const int BS = M * S + 1;
@@ -678,15 +678,17 @@ __global__ void __launch_bounds__(256, 2) k_tridiag_scan(Geometry g, int P, int 
     as[bj * MS + ij] = a[j];
     csm[bj * MS + ij] = c[j];
   }
-  // a CTA owns the S systems kx0 .. kx0+S-1 of one kz; columns past the padded row (pitch) are
-  // not touched, columns in [ncols, pitch) are padding and go back unchanged
-  const int ntile = (g.ncols + S - 1) / S;
+  // a CTA owns the S systems kx0 .. kx0+S-1 of one kz, within the launch's columns
+  // [kx_lo, kx_hi) (kx_lo a multiple of S); columns past the padded row (pitch) are not touched,
+  // columns in [ncols, pitch) are padding and go back unchanged (the last slab copies them)
+  const int ntile = (kx_hi - kx_lo + S - 1) / S;
   const int kz = blockIdx.x / ntile;
-  const int kx0 = (blockIdx.x - kz * ntile) * S;
+  const int kx0 = kx_lo + (blockIdx.x - kz * ntile) * S;
+  const int copy_hi = kx_hi >= g.ncols ? g.pitch : kx_hi;
   const size_t rstride = (size_t)g.nz * g.pitch;
   // ---- coalesced copy-in: thread t copies block t / S of system t % S (S-system row segments)
   const int cpb = threadIdx.x / S, cps = threadIdx.x - cpb * S;
-  const bool cvalid = kx0 + cps < g.pitch;
+  const bool cvalid = kx0 + cps < copy_hi;
   const float2* gsrc = reinterpret_cast<const float2*>(spec) + (size_t)kz * g.pitch + kx0 + cps +
                        (size_t)cpb * M * rstride;
   float2* tsrc = tile + cpb * BS + cps;
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(256, 2) k_tridiag_scan(Geometry g, int P, int 
   const int lseg = b;
   const int kx = kx0 + s;
   const int sys = kz * g.ncols + kx;
-  const bool active = kx < g.ncols && !(kx == 0 && kz == 0) && !is_low(kx, kz, g.nz, low);
+  const bool active = kx < kx_hi && kx < g.ncols && !(kx == 0 && kz == 0) && !is_low(kx, kz, g.nz, low);
   float vL = 0.f, inv = 0.f, X01 = 0.f, X10 = 0.f, tw = 0.f;
   if (P > 1 && active && b < P - 1) {
     const float* t = rtab + ((size_t)sys * (P - 1) + b) * 5;
@@ -973,20 +975,24 @@ cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int par
 }
 
 cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
-                                   cplx<float>* spec, cudaStream_t st) {
+                                   cplx<float>* spec, cudaStream_t st, int kx_lo, int kx_hi) {
   if (!reg_tridiag_ok(g.ny, parts)) return cudaErrorNotSupported;
   const int m = g.ny / parts;
   const int S = reg_systems_per_cta(parts);
-  if (parts <= 32 && (parts & (parts - 1)) == 0) {   // warp-scan variant
+  if (kx_hi < 0) kx_hi = g.ncols;
+  const bool whole = kx_lo == 0 && kx_hi == g.ncols;
+  if (kx_lo < 0 || kx_hi > g.ncols || kx_hi <= kx_lo) return cudaErrorInvalidValue;
+  if (!whole && (!scan_tridiag_ok(g.ny, parts) || kx_lo % S)) return cudaErrorNotSupported;
+  if (scan_tridiag_ok(g.ny, parts)) {   // warp-scan variant
     const int nt = parts * S;
     const size_t smem = (size_t)parts * (m * S + 1) * 8 + (size_t)2 * parts * (m | 1) * 4;
-    const int blocks = g.nz * ((g.ncols + S - 1) / S);
+    const int blocks = g.nz * ((kx_hi - kx_lo + S - 1) / S);
 #define PP_SCAN_CASE(MM)                                                                                       \
   case MM: {                                                                                                   \
     cudaError_t e = prep(k_tridiag_scan<MM>, smem);                                                            \
     if (e != cudaSuccess) return e;                                                                            \
     k_tridiag_scan<MM><<<blocks, nt, smem, st>>>(g, parts, S, low_modes, tb.f.a, tb.f.c, tb.lamx, tb.lamz,     \
-                                                 tb.red_f, spec);                                              \
+                                                 tb.red_f, spec, kx_lo, kx_hi);                                \
     return cudaGetLastError();                                                                                 \
   }
     switch (m) {

@@ -9,7 +9,9 @@
 //
 // The array lives in every GPU that loads the library until the process exits.  In host code
 // its name only stands for the device object; the device address is obtained once per device
-// with cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// with cudaGetSymbolAddress (with that device current, under a lock) and passed to the kernels.
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -19,11 +21,13 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_ws[kStaticWorkspaceBytes];
 
+std::mutex g_static_mu;                          // guards the per-device address cache
 unsigned char* g_static_ptr[kMaxDevices] = {};   // device address of g_static_ws, per device
 
 poisson_status static_workspace_address(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);   // first calls from several threads look it up once
   if (!g_static_ptr[dev]) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_static_ws) != cudaSuccess || !ptr) return PS_ECUDA;
@@ -39,6 +43,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 extern "C" poisson_status poisson_solve_static_ws(poisson_plan_t pl, const void* rhs, void* p, void* stream) {
   if (!pl || !rhs || !p) return PS_EINVAL;
+  if (!pl->children.empty()) return PS_EINVAL;   // batched plans have no geometry of their own
   if (!aligned16(rhs) || !aligned16(p)) return PS_EINVAL;
   if (pl->ws_bytes > kStaticWorkspaceBytes) return PS_EUNSUPPORTED;   // grid too large for the array
   if (pl->precision == PP_FP32_REFINED && rhs == p) return PS_EINVAL;
@@ -47,7 +52,9 @@ extern "C" poisson_status poisson_solve_static_ws(poisson_plan_t pl, const void*
   if (s != PS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps whatever the previous call left: reload this plan's tables, rebuild its
-  // FP64 PDD factors and clear the status word (the only region that must start at zero).
+  // PDD factors and clear the status word (the only region that must start at zero).  The
+  // table image is ordinary (pageable) host memory, so this copy returns only once the stream
+  // has reached it.
   if (cudaMemcpyAsync(ws + pl->off_tables, pl->host_tables.data(), pl->host_tables.size(),
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
     return PS_ECUDA;

@@ -337,4 +337,89 @@ __device__ __forceinline__ float2 resid_pair_line(const ResidLine& R, int n) {
   return make_float2(out[0], out[1]);
 }
 
+// ---- the same residual with the two cells of a pair in packed FP32x2 operations ------------
+// Each FP32x2 instruction performs the same correctly rounded operation on both lanes (cell 0
+// in .x, cell 1 in .y), so the double-float algorithms below are those of resid_pair_line
+// applied lane by lane, at half the issued instructions.  The *_rn intrinsics are never fused
+// into FMAs by the compiler, which the error-free transformations rely on.
+struct df2 { float2 hi, lo; };
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one FMA with the multiplier -1 (exact product, one rounding: the correctly rounded
+// difference)
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// TwoSum / TwoDiff (Knuth) lane by lane: hi + lo == a +- b exactly.
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = f2add(a, b);
+  const float2 bp = f2sub(s, a);
+  return df2{s, f2add(f2sub(a, f2sub(s, bp)), f2sub(b, bp))};
+}
+__device__ __forceinline__ df2 two_diff2(float2 a, float2 b) {
+  const float2 s = f2sub(a, b);
+  const float2 bp = f2sub(s, a);
+  return df2{s, f2sub(f2sub(a, f2sub(s, bp)), f2add(b, bp))};
+}
+__device__ __forceinline__ df2 diff_sum2(df2 a, df2 b) {
+  const df2 s = two_sum2(a.hi, b.hi);
+  return df2{s.hi, f2add(s.lo, f2add(a.lo, b.lo))};
+}
+// (S, C) -= coef * (d.hi + d.lo), compensated (Dot2), coef a double-float broadcast to both lanes.
+__device__ __forceinline__ void dot2_sub2(float2& S, float2& C, float2 ch, float2 cl, df2 d) {
+  const float2 p = f2mul(ch, d.hi);
+  float2 q = f2fma(ch, d.hi, make_float2(-p.x, -p.y));
+  q = f2fma(cl, d.hi, q);
+  q = f2fma(ch, d.lo, q);
+  const df2 s = two_diff2(S, p);
+  S = s.hi;
+  C = f2add(C, f2sub(s.lo, q));
+}
+
+__device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
+  const int i0 = 2 * n;
+  const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
+  const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
+  const float2 pc = ld_f2(R.P + i0);
+  const float pm = R.P[im], pp = R.P[ip];
+  const float2 zm = ld_f2(R.Pzm + i0), zp = ld_f2(R.Pzp + i0);
+  const float2 ym = R.Pym ? ld_f2(R.Pym + i0) : make_float2(0.f, 0.f);
+  const float2 yp = R.Pyp ? ld_f2(R.Pyp + i0) : make_float2(0.f, 0.f);
+  const double2 fv = *reinterpret_cast<const double2*>(R.f + i0);
+  // x-neighbours: cell 0 pairs (p_{i-1}, p_{i+1} = cell 1), cell 1 pairs (p_{i+2}, p_i = cell 0);
+  // the difference between the two cells is shared with opposite signs
+  df2 dout = two_diff2(make_float2(pm, pp), pc);
+  const df2 d01 = two_diff2(make_float2(pc.y, pc.x), pc);   // (p1 - p0, p0 - p1), exact
+  df2 dz0 = two_diff2(zp, pc), dz1 = two_diff2(zm, pc);
+  df2 dy0 = two_diff2(ym, pc), dy1 = two_diff2(yp, pc);
+  if (R.Q) {
+    const float2 qc = ld_f2(R.Q + i0);
+    const float qm = R.Q[im], qp = R.Q[ip];
+    const float2 qzm = ld_f2(R.Qzm + i0), qzp = ld_f2(R.Qzp + i0);
+    const float2 qym = R.Qym ? ld_f2(R.Qym + i0) : make_float2(0.f, 0.f);
+    const float2 qyp = R.Qyp ? ld_f2(R.Qyp + i0) : make_float2(0.f, 0.f);
+    dout = diff_sum2(dout, two_diff2(make_float2(qm, qp), qc));
+    const df2 q01 = two_diff2(make_float2(qc.y, qc.x), qc);
+    const df2 e01 = diff_sum2(d01, q01);
+    dz0 = diff_sum2(dz0, two_diff2(qzp, qc));
+    dz1 = diff_sum2(dz1, two_diff2(qzm, qc));
+    if (R.Qym) dy0 = diff_sum2(dy0, two_diff2(qym, qc));
+    if (R.Qyp) dy1 = diff_sum2(dy1, two_diff2(qyp, qc));
+    dout = diff_sum2(dout, e01);
+  } else {
+    dout = diff_sum2(dout, d01);
+  }
+  float2 fh, fl;
+  f64_split(fv.x, fh.x, fl.x);
+  f64_split(fv.y, fh.y, fl.y);
+  const df2 s0 = two_sum2(fh, make_float2(-R.mh, -R.mh));
+  float2 S = s0.hi, C = f2add(s0.lo, f2sub(fl, make_float2(R.ml, R.ml)));
+  dot2_sub2(S, C, make_float2(R.cx.hi, R.cx.hi), make_float2(R.cx.lo, R.cx.lo), dout);
+  dot2_sub2(S, C, make_float2(R.cz.hi, R.cz.hi), make_float2(R.cz.lo, R.cz.lo), diff_sum2(dz0, dz1));
+  if (R.Pym) dot2_sub2(S, C, make_float2(R.ca.hi, R.ca.hi), make_float2(R.ca.lo, R.ca.lo), dy0);
+  if (R.Pyp) dot2_sub2(S, C, make_float2(R.cc.hi, R.cc.hi), make_float2(R.cc.lo, R.cc.lo), dy1);
+  return f2add(S, C);
+}
+
 }  // namespace pp

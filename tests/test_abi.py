@@ -117,3 +117,33 @@ def test_selftest_flag_is_accepted_by_the_planner(native):
     d, _ = _desc(native, nx=512, ny=4, nz=16, faces=W.tanh_faces(4, 1.5), precision=2,
                  flags=native.POISSON_SELFTEST_WAIT)
     assert _create(native, d)[0] == 0
+
+
+def test_slab_chain_configuration_is_validated_on_the_host(native):
+    """poisson_plan_set_chain accepts only the FP32 scan-PDD path with tile-aligned slab widths;
+    single-stream configurations make no CUDA call."""
+    L = native.lib()
+
+    def plan(**kw):
+        d, arr = _desc(native, **kw)
+        h = ctypes.c_void_p()
+        assert L.poisson_plan_create(ctypes.byref(d), ctypes.byref(h)) == 0
+        return h, arr
+
+    f96 = W.tanh_faces(96, 2.0)
+    h64, _ = plan(nx=96, ny=96, nz=64, faces=f96, precision=0, pdd_parts=8)
+    h32, _ = plan(nx=96, ny=96, nz=64, faces=f96, precision=1, pdd_parts=16)
+    hreg, _ = plan(nx=96, ny=96, nz=64, faces=f96, precision=1, pdd_parts=48)   # register kernel
+    try:
+        assert L.poisson_plan_set_chain(h64, 32, 1) == native.PS_EUNSUPPORTED
+        assert L.poisson_plan_set_chain(hreg, 32, 1) == native.PS_EUNSUPPORTED
+        assert L.poisson_plan_set_chain(h32, 32, 1) == native.PS_OK      # z tile 32, 16 systems per CTA
+        assert L.poisson_plan_set_chain(h32, 16, 1) == native.PS_EUNSUPPORTED
+        assert L.poisson_plan_set_chain(h32, 48, 1) == native.PS_EUNSUPPORTED
+        assert L.poisson_plan_set_chain(h32, 32, 3) == native.PS_EINVAL
+        assert L.poisson_plan_set_chain(h32, -1, 1) == native.PS_EINVAL
+        assert L.poisson_plan_set_chain(h32, 0, 1) == native.PS_OK
+        assert L.poisson_plan_set_chain(None, 32, 1) == native.PS_EINVAL
+    finally:
+        for h in (h64, h32, hreg):
+            L.poisson_plan_destroy(h)

@@ -218,6 +218,50 @@ def test_nonfinite_input_sets_device_status(P):
     assert plan.device_status() == 0
 
 
+@pytest.mark.parametrize("prec,comp", [(0, "v"), (0, "w"), (1, "v"), (2, "w")])
+def test_nonfinite_velocity_component_sets_device_status(P, prec, comp):
+    """POISSON_CHECK_FINITE scans every velocity component of the projection, not only u."""
+    nx, ny, nz = 16, 8, 8
+    plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=prec, pdd_parts=2, flags=P.POISSON_CHECK_FINITE,
+                  device=DEV)
+    dtype = torch.float32 if prec == 1 else torch.float64
+    u, v, w = (to_dev(a, dtype) for a in W.random_velocity(7, nx, ny, nz))
+    {"v": v, "w": w}[comp][3, 2, 5] = float("nan")
+    p = torch.empty(ny, nz, nx, dtype=dtype, device=DEV)
+    plan.project(u, v, w, 1e-3, p_out=p)
+    assert plan.device_status() == 6
+    u, v, w = (to_dev(a, dtype) for a in W.random_velocity(7, nx, ny, nz))
+    plan.project(u, v, w, 1e-3, p_out=p)
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("nx,ny,nz,parts,steps,tol", [(48, 24, 36, 4, 2, 1e-12), (64, 32, 54, 2, 1, 2e-9)])
+def test_fp32_refined_projection_matches_oracle(P, nx, ny, nz, parts, steps, tol):
+    """projection_step of PP_FP32_REFINED plans: pairs, double-float divergence, refined solve, gradient."""
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.random_velocity(8, nx, ny, nz)
+    dt = 2e-3
+    want = oracle.project(g, u, v, w, dt)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=parts, fp64_low_modes=4,
+                  refine_steps=steps, device=DEV)
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    pt = plan.project(ut, vt, wt, dt)
+    torch.cuda.synchronize()
+    for got, ref in zip((ut, vt, wt, pt), want):
+        assert relerr(got.cpu().numpy(), ref) <= tol
+    # the fields round-trip through FP32 pairs (48-bit significands): the wall faces of v keep
+    # their values to 2^-48 relative
+    for wall in (0, -1):
+        assert np.max(np.abs(vt[wall].cpu().numpy() - v[wall])) <= 2.0 ** -47 * np.max(np.abs(v))
+    from paper_2104_08863_gb300 import _native
+    L = _native.lib()
+    st = torch.cuda.current_stream().cuda_stream
+    assert L.projection_step(plan._h, ut.data_ptr(), vt.data_ptr(), wt.data_ptr(), 0, dt, st) == _native.PS_EINVAL
+    assert L.projection_step(plan._h, ut.data_ptr(), vt.data_ptr(), wt.data_ptr(), ut.data_ptr(), dt, st) == \
+        _native.PS_EINVAL
+
+
 def test_bad_arguments_are_rejected(P):
     nx, ny, nz = 8, 8, 8
     plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=P.PP_FP64, device=DEV)
