@@ -13,6 +13,7 @@
 #include <utility>
 
 #include "fft_static.cuh"
+#include "k_fft_x_reg.cuh"
 #include "xline.cuh"
 
 namespace pp {
@@ -325,9 +326,75 @@ inline cudaError_t set_smem(K kernel, int smem) {
   return ensure_smem_limit((const void*)kernel, (size_t)smem);
 }
 
+// FP32 spectra of FP32 fields: the two-pass register kernels (k_fft_x_reg.cuh).  With FP64
+// fields (the FP64 right-hand side, the refinement residual, the FP64 assembly of the refined
+// pressure) the Stockham kernels measured faster: their epilogues are latency-bound and want the
+// occupancy that the register kernels (up to 128 registers per thread) do not leave.
+template <typename TI, int M>
+cudaError_t launch_fwd_x_reg(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
+                             cplx<float>* spec, cudaStream_t st) {
+  using C = XReg<M>;
+  const int nlines = g.ny * g.nz;
+  const dim3 grid((nlines + C::LPB - 1) / C::LPB);
+  cudaError_t e = cudaSuccess;
+#define PP_FWDR(MODEV)                                                                  \
+  {                                                                                     \
+    auto k = k_fwd_x_reg<TI, M, MODEV>;                                                 \
+    if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                            \
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, args, tb.f, tb, spec, nlines);              \
+  }
+  switch (mode) {
+    case FWD_PLAIN: PP_FWDR(FWD_PLAIN) break;
+    case FWD_DIV: PP_FWDR(FWD_DIV) break;
+    case FWD_GRADT: PP_FWDR(FWD_GRADT) break;
+    default: return cudaErrorNotSupported;
+  }
+#undef PP_FWDR
+  return cudaGetLastError();
+}
+
+template <typename TO, int M>
+cudaError_t launch_inv_x_reg(const Geometry& g, const DevTables& tb, InvMode mode, const cplx<float>* spec, TO* out,
+                             double scale, bool accumulate, cudaStream_t st, PairArgs pair) {
+  using C = XReg<M>;
+  const int nlines = g.ny * g.nz;
+  const dim3 grid((nlines + C::LPB - 1) / C::LPB);
+  cudaError_t e = cudaSuccess;
+#define PP_INVR(MODEV, ACCV)                                                                       \
+  {                                                                                                \
+    auto k = k_inv_x_reg<TO, M, MODEV, ACCV>;                                                      \
+    if ((e = set_smem(k, C::SMEM)) != cudaSuccess) return e;                                       \
+    k<<<grid, C::THREADS, C::SMEM, st>>>(g, tb.f, spec, out, scale, nlines, tb.dy, tb.acc, pair); \
+  }
+  if (mode == INV_ACCUM) {
+    if (accumulate) PP_INVR(INV_ACCUM, true) else PP_INVR(INV_ACCUM, false)
+  } else if (mode == INV_STORE) {
+    if (accumulate) PP_INVR(INV_STORE, true) else PP_INVR(INV_STORE, false)
+  } else {
+    return cudaErrorNotSupported;
+  }
+#undef PP_INVR
+  return cudaGetLastError();
+}
+
+template <typename T, typename TI, int M>
+cudaError_t launch_fwd_x_stockham(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
+                                  const FwdArgs& args, cplx<T>* spec, cudaStream_t st);
+
 template <typename T, typename TI, int M>
 cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
                            const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 4) {
+    return launch_fwd_x_reg<TI, M>(g, tb, mode, args, spec, st);
+  } else {
+    return launch_fwd_x_stockham<T, TI, M>(g, tb, tt, mode, args, spec, st);
+  }
+}
+
+// FP64 spectra and FP64 fields: the Stockham kernels above.
+template <typename T, typename TI, int M>
+cudaError_t launch_fwd_x_stockham(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
+                                  const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
   using C = XTile<T, M>;
   const int nlines = g.ny * g.nz;
   const dim3 grid((nlines + C::LPB - 1) / C::LPB);
@@ -372,9 +439,9 @@ cudaError_t launch_fwd_x_m(const Geometry& g, const DevTables& tb, const Tables<
 }
 
 template <typename T, typename TO, int M>
-cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
-                           const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
-                           PairArgs pair) {
+cudaError_t launch_inv_x_stockham(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
+                                  const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                                  PairArgs pair) {
   using C = XTile<T, M>;
   const int nlines = g.ny * g.nz;
   const dim3 grid((nlines + C::LPB - 1) / C::LPB);
@@ -398,6 +465,17 @@ cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<
   }
 #undef PP_INVF
   return cudaGetLastError();
+}
+
+template <typename T, typename TO, int M>
+cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<T>& tt, InvMode mode,
+                           const cplx<T>* spec, TO* out, double scale, bool accumulate, cudaStream_t st,
+                           PairArgs pair) {
+  if constexpr (sizeof(T) == 4 && sizeof(TO) == 4) {
+    return launch_inv_x_reg<TO, M>(g, tb, mode, spec, out, scale, accumulate, st, pair);
+  } else {
+    return launch_inv_x_stockham<T, TO, M>(g, tb, tt, mode, spec, out, scale, accumulate, st, pair);
+  }
 }
 
 #define PP_X_SIZES(F) F(16) F(32) F(48) F(64) F(96) F(128) F(192) F(256) F(384) F(512) F(768) F(1024)

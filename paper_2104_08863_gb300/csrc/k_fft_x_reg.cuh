@@ -1,0 +1,176 @@
+// Two-pass register x-transforms for FP32 spectra of FP32 fields (steps (2) and (8) of Sec. 3.2).
+//
+// The half-length complex transform of a line (M = Nx/2 = N1 x N2, N1 >= N2, both <= 32) is done
+// by threads that each hold a whole short transform in registers: pass 1 thread (t, n1) of line
+// t produces z[n1 + N1 n2] for n2 < N2 directly from the field (the right-hand side producer of
+// the mode: a plain load, the divergence of Eq. 7, the adjoint's G^T g), takes their
+// N2-point DFT, multiplies output k2 by W_M^{n1 k2} and writes it to shared memory at
+// [t][k2][n1]; pass 2 thread (t, k2) takes the N1-point DFT of row k2 (output k1 is Z[k2 + N2 k1]).
+// Forward: the Z are written back in natural order and the Nx/2+1 spectral bins unpacked from
+// Z_k and Z_{M-k} (fwd_post) and stored.  Inverse: pass 1 packs X_k and X_{M-k} (inv_pre) on the
+// way in, pass 2 writes (or adds) the real values straight from registers, with the line's
+// dy-weighted sum when asked.  Against the Stockham kernels this makes
+// one (inverse) or two (forward) shared-memory round trips instead of one per stage plus two, and
+// every index is a compile-time constant.  Row k2 of a line's buffer has an odd stride B = N1 + 1
+// (in complex values), so the pass-2 reads of consecutive k2 fall on distinct bank pairs.
+#pragma once
+
+#include "fft_reg.cuh"
+#include "xline.cuh"
+
+namespace pp {
+
+template <int M> struct XReg {
+  static constexpr int N1 = split_n1(M), N2 = M / N1;
+  static constexpr int LPB0 = 256 / N1;
+  static constexpr int LPB = LPB0 < 1 ? 1 : (LPB0 > 32 ? 32 : LPB0);
+  static constexpr int THREADS = LPB * N1;
+  static constexpr int B = N1 % 2 == 0 ? N1 + 1 : N1;
+  static constexpr int LS = N2 * B > M ? N2 * B : M;   // per-line stride (>= M for the natural order)
+  static constexpr int SMEM = LPB * LS * (int)sizeof(cplx<float>);
+  static_assert(N1 * N2 == M && N1 <= 32 && N2 <= 32, "split");
+  static_assert(B % 2 == 1, "odd row stride");
+};
+
+// Forward x-transform of an FP32 field into the FP32 half spectrum; MODE as in fwd_load
+// (FWD_PLAIN, FWD_DIV, FWD_GRADT).
+template <typename TI, int M, int MODE>
+__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+    k_fwd_x_reg(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
+                int nlines) {
+  using C = XReg<M>;
+  constexpr int N1 = C::N1, N2 = C::N2, LPB = C::LPB, B = C::B, LS = C::LS, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int line0 = blockIdx.x * LPB;
+  {
+    const int t = threadIdx.x / N1, n1 = threadIdx.x - t * N1;
+    const int line = line0 + t;
+    cplx<float> v[N2];
+    if (line < nlines) {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = fwd_load<float, TI, MODE>(g, args, tt, tb, line, n1 + N1 * n2);
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = mk<float>(0.f, 0.f);
+    }
+    reg_dft<float, N2, -1>(v);
+    cplx<float>* row = buf + t * LS + n1;
+    static_for<0, N2>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int k2 = reg_freq(N2, s);
+      cplx<float> x = v[s];
+      if constexpr (k2 != 0) x = cmul(x, ldg_c(tt.tw_m + n1 * k2));
+      row[k2 * B] = x;
+    });
+  }
+  __syncthreads();
+  constexpr int P2 = LPB * N2;   // pass-2 threads
+  cplx<float> u[N1];
+  const int t2 = threadIdx.x / N2, k2 = threadIdx.x - t2 * N2;
+  if (threadIdx.x < P2) {
+    const cplx<float>* row = buf + t2 * LS + k2 * B;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = row[n1];
+    reg_dft<float, N1, -1>(u);
+  }
+  __syncthreads();
+  if (threadIdx.x < P2) {
+    cplx<float>* nat = buf + t2 * LS + k2;
+    static_for<0, N1>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      nat[N2 * reg_freq(N1, s)] = u[s];
+    });
+  }
+  __syncthreads();
+  constexpr int M1 = M + 1;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
+    const int t = idx / M1, kx = idx - t * M1;
+    const int line = line0 + t;
+    if (line >= nlines) continue;
+    const cplx<float>* nat = buf + t * LS;
+    const cplx<float> Zk = nat[kx == M ? 0 : kx];
+    const cplx<float> Zc = conj(nat[kx == 0 ? 0 : M - kx]);
+    st_c(spec + (size_t)line * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+  }
+}
+
+// Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE
+// (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1].
+template <typename TO, int M, int MODE, bool ACC>
+__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+    k_inv_x_reg(Geometry g, Tables<float> tt, const cplx<float>* __restrict__ spec, TO* __restrict__ out, double scl,
+                int nlines, const double* __restrict__ dy, double* __restrict__ acc, PairArgs pair) {
+  using C = XReg<M>;
+  constexpr int N1 = C::N1, N2 = C::N2, LPB = C::LPB, B = C::B, LS = C::LS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int line0 = blockIdx.x * LPB;
+  {
+    const int t = threadIdx.x / N1, n1 = threadIdx.x - t * N1;
+    const int line = line0 + t;
+    cplx<float> v[N2];
+    if (line < nlines) {
+      const cplx<float>* X = spec + (size_t)line * g.pitch;
+      cplx<float> xk[N2], xm[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const int n = n1 + N1 * n2;
+        xk[n2] = ld_c(X + n);
+        xm[n2] = ld_c(X + (M - n));
+      }
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const int n = n1 + N1 * n2;
+        v[n2] = inv_pre(n, xk[n2], xm[n2], ldg_c(tt.tw_post + n));
+      }
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = mk<float>(0.f, 0.f);
+    }
+    reg_dft<float, N2, 1>(v);
+    cplx<float>* row = buf + t * LS + n1;
+    static_for<0, N2>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int k2 = reg_freq(N2, s);
+      cplx<float> x = v[s];
+      if constexpr (k2 != 0) x = cmulc(x, ldg_c(tt.tw_m + n1 * k2));
+      row[k2 * B] = x;
+    });
+  }
+  __syncthreads();
+  constexpr int P2 = LPB * N2;
+  const int t2 = threadIdx.x / N2, k2 = threadIdx.x - t2 * N2;
+  const int line = line0 + t2;
+  const bool act = threadIdx.x < P2 && line < nlines;
+  double wsum = 0.0;
+  if (act) {
+    cplx<float> u[N1];
+    const cplx<float>* row = buf + t2 * LS + k2 * B;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = row[n1];
+    reg_dft<float, N1, 1>(u);
+    const float s = float(scl);
+    TO* o = out + (size_t)line * g.nx + 2 * k2;
+    float hs = 0.f, hc = 0.f;
+    static_for<0, N1>([&](auto sc) {
+      constexpr int sl = decltype(sc)::value;
+      constexpr int k1 = reg_freq(N1, sl);
+      const float x0 = u[sl].x * s, x1 = u[sl].y * s;
+      inv_store<float, TO, MODE>(o + 2 * N2 * k1, 0, x0, x1, pair);
+      if constexpr (ACC) {
+        acc_add(hs, hc, x0);
+        acc_add(hs, hc, x1);
+      }
+    });
+    if constexpr (ACC) wsum = dy[line / g.nz] * ((double)hs + (double)hc);
+  }
+  if constexpr (ACC) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if ((threadIdx.x & 31) == 0 && wsum != 0.0) atomicAdd(acc + 1, wsum);
+  }
+}
+
+}  // namespace pp
