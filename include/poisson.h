@@ -127,6 +127,14 @@ poisson_status poisson_solve_adjoint(poisson_plan_t plan, const void* g, void* q
 poisson_status projection_step(poisson_plan_t plan, void* u, void* v, void* w, void* p_out,
                                double dt, void* stream);
 
+/* The right-hand side of the pressure equation as a field: f = D(u)/dt (Eq. 7), the discrete
+ * divergence of the staggered velocity at the cell centres, with the grid metrics of the plan.
+ * u, w: device [ny][nz][nx]; v: device [ny+1][nz][nx]; f: device [ny][nz][nx], distinct from
+ * u, v and w; dtype as for poisson_solve (FP64 for PP_FP64 and PP_FP32_REFINED, FP32 for
+ * PP_FP32), computed in that precision.  dt > 0.  One kernel launch on `stream`. */
+poisson_status poisson_divergence(poisson_plan_t plan, const void* u, const void* v, const void* w, void* f,
+                                  double dt, void* stream);
+
 /* Adjoint of the velocity map of projection_step (which does not depend on dt):
  * g <- g - D^T S^T G^T g in place, S the gauged solve.  Uses the same FFT and PDD kernels:
  * L_h^T = W L_h W^-1 with W = diag(dy_j), so the transposed solve is a forward solve of a
@@ -234,6 +242,13 @@ poisson_status poisson_autotune(const poisson_desc* desc, void* stream, int* pdd
  * the plan's device current (the second stream is created then); results are identical to the
  * whole-spectrum order. */
 poisson_status poisson_plan_set_chain(poisson_plan_t plan, int slab_cols, int streams);
+
+/* Diagnostics: the FP64 fused multiply-add throughput of the current device, in GFLOP/s (2 flops
+ * per FMA), measured by a kernel of independent FMA chains on every SM, timed with events on
+ * `stream` (best of three launches after one warm-up; synchronises `stream`).  It is the
+ * denominator of the roofline of FP64-arithmetic-bound kernels.  scratch: caller-owned device
+ * memory of at least 8 * 256 * 8 * (multiprocessor count) bytes (receives the chains' sums). */
+poisson_status poisson_fp64_fma_rate(void* scratch, size_t bytes, void* stream, double* gflops);
 
 /* Synchronise `stream` and read the device status word (PS_OK, PS_ENONFINITE, ...),
  * then clear it. */

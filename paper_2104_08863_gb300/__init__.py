@@ -17,7 +17,7 @@ from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_
                       POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, POISSON_SELFTEST_WAIT, PoissonError,
                       check)
 
-__all__ = ["Plan", "BatchPlan", "autotune", "tune_batch", "ProjectionFn", "PoissonError", "POISSON_GENERIC_FFT", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
+__all__ = ["Plan", "BatchPlan", "autotune", "tune_batch", "fp64_fma_rate", "ProjectionFn", "PoissonError", "POISSON_GENERIC_FFT", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
            "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "PT_PDD_TRUNCATED", "POISSON_CHECK_FINITE", "POISSON_TIMING",
            "POISSON_SELFTEST_WAIT"]
 
@@ -172,6 +172,18 @@ class Plan:
             _ptr(u_d), _ptr(v_d), _ptr(w_d), _ptr(p_d) if p_d is not None else 0, float(dt), _stream(stream)),
             "projection_step_host")
 
+    def divergence(self, u, v, w, dt: float = 1.0, out=None, stream=None) -> torch.Tensor:
+        """f = D(u)/dt (Eq. 7) on the cell centres (poisson_divergence)."""
+        self._check(u, self.cell_shape, "u")
+        self._check(v, self.v_shape, "v")
+        self._check(w, self.cell_shape, "w")
+        if out is None:
+            out = torch.empty_like(u)
+        self._check(out, self.cell_shape, "out")
+        check(_native.lib().poisson_divergence(self._h, _ptr(u), _ptr(v), _ptr(w), _ptr(out), float(dt),
+                                               _stream(stream)), "poisson_divergence")
+        return out
+
     def set_chain(self, slab_cols: int, streams: int = 1):
         """Run the FP32 z-transform / wall-normal / inverse z-transform passes in kx slabs of
         slab_cols columns (0: whole spectrum) over 1 or 2 streams (poisson_plan_set_chain)."""
@@ -199,6 +211,18 @@ class Plan:
         if h is not None and _native._LIB is not None:
             _native._LIB.poisson_plan_destroy(h)
             self._h = None
+
+
+def fp64_fma_rate(device=None) -> float:
+    """FP64 FMA throughput of the device in GFLOP/s (poisson_fp64_fma_rate; diagnostics)."""
+    dev = torch.device(device if device is not None else "cuda")
+    with torch.cuda.device(dev):
+        props = torch.cuda.get_device_properties(dev)
+        scratch = torch.empty(8 * 256 * 8 * props.multi_processor_count, dtype=torch.uint8, device=dev)
+        out = ctypes.c_double()
+        check(_native.lib().poisson_fp64_fma_rate(scratch.data_ptr(), scratch.numel(), _stream(), ctypes.byref(out)),
+              "poisson_fp64_fma_rate")
+    return float(out.value)
 
 
 def _desc(nx, ny, nz, faces, lx, lz, precision, tridiag, pdd_parts, fp64_low_modes, refine_steps, flags):

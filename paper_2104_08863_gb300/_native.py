@@ -26,7 +26,8 @@ EXPORTS = (
     "poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
     "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
     "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
-    "projection_timestep", "projection_timestep_host", "poisson_plan_set_chain", "poisson_device_status",
+    "projection_timestep", "projection_timestep_host", "poisson_divergence", "poisson_plan_set_chain",
+    "poisson_fp64_fma_rate", "poisson_device_status",
     "poisson_last_launch_count", "poisson_stage_times", "poisson_plan_destroy", "poisson_status_string",
 )
 
@@ -77,6 +78,8 @@ def lib() -> ctypes.CDLL:
     L.projection_timestep.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
     L.projection_timestep_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, d, vp]
     L.poisson_plan_set_chain.argtypes = [vp, i, i]
+    L.poisson_divergence.argtypes = [vp, vp, vp, vp, vp, d, vp]
+    L.poisson_fp64_fma_rate.argtypes = [vp, sz, vp, ctypes.POINTER(d)]
     L.poisson_device_status.argtypes = [vp, vp]
     L.poisson_last_launch_count.argtypes = [vp]
     L.poisson_last_launch_count.restype = i
@@ -88,7 +91,8 @@ def lib() -> ctypes.CDLL:
     for name in ("poisson_plan_create", "poisson_workspace_size", "poisson_set_workspace", "poisson_solve",
                  "poisson_solve_adjoint", "poisson_solve_static_ws", "poisson_plan_batched", "poisson_solve_batched", "poisson_autotune",
                  "projection_step", "projection_step_adjoint", "projection_step_host", "momentum_predictor",
-                 "projection_timestep", "projection_timestep_host", "poisson_plan_set_chain", "poisson_device_status",
+                 "projection_timestep", "projection_timestep_host", "poisson_divergence", "poisson_plan_set_chain",
+                 "poisson_fp64_fma_rate", "poisson_device_status",
                  "poisson_plan_destroy"):
         getattr(L, name).restype = i
     _LIB = L

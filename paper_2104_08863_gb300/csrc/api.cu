@@ -876,6 +876,26 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   return PS_OK;
 }
 
+poisson_status poisson_divergence(poisson_plan_t pl, const void* u, const void* v, const void* w, void* f, double dt,
+                                  void* stream) {
+  if (!pl || !u || !v || !w || !f) return PS_EINVAL;
+  if (!pl->children.empty()) return PS_EINVAL;
+  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!(dt > 0.0) || !isfinite(dt)) return PS_EINVAL;
+  if (!aligned16(u) || !aligned16(v) || !aligned16(w) || !aligned16(f)) return PS_EINVAL;
+  if (f == u || f == v || f == w) return PS_EINVAL;
+  pl->launches = 0;
+  pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, (cudaStream_t)stream, (pl->flags & POISSON_TIMING) != 0};
+  if (pl->precision == PP_FP32)
+    PP_TRY_N("divergence", launch_divergence<float>(pl->g, ex.dt, (const float*)u, (const float*)v, (const float*)w,
+                                                    (float*)f, dt, ex.st));
+  else
+    PP_TRY_N("divergence", launch_divergence<double>(pl->g, ex.dt, (const double*)u, (const double*)v,
+                                                     (const double*)w, (double*)f, dt, ex.st));
+  return PS_OK;
+}
+
 poisson_status poisson_plan_set_chain(poisson_plan_t pl, int slab_cols, int streams) {
   if (!pl || !pl->children.empty() || slab_cols < 0 || streams < 1 || streams > 2) return PS_EINVAL;
   if (slab_cols == 0) {

@@ -195,6 +195,11 @@ cudaError_t launch_weighted_pair(const Geometry& g, const DevTables& tb, const f
 template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st);
 
+// f = D(u)/dt (Eq. 7) as a cell field, in T arithmetic.
+template <typename T>
+cudaError_t launch_divergence(const Geometry& g, const DevTables& tb, const T* u, const T* v, const T* w, T* f,
+                              double dt, cudaStream_t st);
+
 // One stage of Heun's RK2 momentum predictor (csrc/k_momentum.cu):
 //   out = alpha * base + beta * s + bdt * R(s),  R = -div(s s) + nu lap(s) + (fx, 0, 0).
 // base may be null (alpha = 0); out may alias base but not s.

@@ -7,6 +7,8 @@
 //                L_h^T = W L_h W^-1 and the forward gauge (zero dy-weighted mean of p') is the
 //                zero-sum gauge of q.
 //  k_check_finite : sets the device status word when a value is NaN or Inf.
+//  k_divergence : f = D(u)/dt of Eq. 7 on the cell centres (the right-hand side of the
+//                pressure equation), for callers that want it as a field.
 #include "fpconv.cuh"
 #include "internal.h"
 
@@ -99,6 +101,28 @@ __global__ void k_check_finite(const T* __restrict__ x, size_t n, int* status) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(status, (int)DEV_NONFINITE);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_divergence(Geometry g, const T* __restrict__ u, const T* __restrict__ v,
+                                                    const T* __restrict__ w, T* __restrict__ f,
+                                                    const T* __restrict__ inv_dy, T inv_dt) {
+  const size_t plane = (size_t)g.nz * g.nx;
+  const int nlines = g.ny * g.nz;
+  const T ix = T(1.0 / g.dx), iz = T(1.0 / g.dz);
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
+    const int j = line / g.nz, k = line - j * g.nz;
+    const T iy = inv_dy[j];
+    const size_t row = (size_t)line * g.nx;
+    const size_t rkp = (size_t)j * plane + (size_t)(k + 1 == g.nz ? 0 : k + 1) * g.nx;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const size_t idx = row + i;
+      const T dux = u[row + (i + 1 == g.nx ? 0 : i + 1)] - u[idx];
+      const T dvy = v[idx + plane] - v[idx];
+      const T dwz = w[rkp + i] - w[idx];
+      f[idx] = (dux * ix + dvy * iy + dwz * iz) * inv_dt;
+    }
+  }
+}
+
 static int stream_grid(size_t total) {
   size_t blocks = (total + 255) / 256;
   const size_t cap = 152 * 16;
@@ -148,6 +172,15 @@ cudaError_t launch_weighted_pair(const Geometry& g, const DevTables& tb, const f
 }
 
 template <typename T>
+cudaError_t launch_divergence(const Geometry& g, const DevTables& tb, const T* u, const T* v, const T* w, T* f,
+                              double dt, cudaStream_t st) {
+  const int nlines = g.ny * g.nz, cap = 152 * 16;
+  const T* inv_dy = sizeof(T) == 8 ? (const T*)tb.d.inv_dy : (const T*)tb.f.inv_dy;
+  k_divergence<T><<<nlines < cap ? nlines : cap, line_block(g), 0, st>>>(g, u, v, w, f, inv_dy, T(1.0 / dt));
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t st) {
   k_check_finite<T><<<stream_grid(n), 256, 0, st>>>(x, n, status);
   return cudaGetLastError();
@@ -165,7 +198,64 @@ template cudaError_t launch_scale_planes<double>(const Geometry&, const DevTable
                                                  cudaStream_t);
 template cudaError_t launch_scale_planes<float>(const Geometry&, const DevTables&, const float*, float*, bool,
                                                 cudaStream_t);
+template cudaError_t launch_divergence<double>(const Geometry&, const DevTables&, const double*, const double*,
+                                               const double*, double*, double, cudaStream_t);
+template cudaError_t launch_divergence<float>(const Geometry&, const DevTables&, const float*, const float*,
+                                              const float*, float*, double, cudaStream_t);
 template cudaError_t launch_check_finite<double>(const double*, size_t, int*, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, size_t, int*, cudaStream_t);
 
 }  // namespace pp
+
+// ---- FP64 FMA throughput (diagnostics) --------------------------------------------------------
+// Each thread runs 8 independent chains of dependent FMAs (enough in flight per warp to fill the
+// FP64 pipe); the sum is stored so that the chains are not removed.
+namespace pp {
+__global__ void __launch_bounds__(256) k_fp64_fma_rate(double* __restrict__ out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+  double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+}  // namespace pp
+
+extern "C" poisson_status poisson_fp64_fma_rate(void* scratch, size_t bytes, void* stream, double* gflops) {
+  if (!scratch || !gflops) return PS_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PS_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PS_ECUDA;
+  const int blocks = sms * 8, threads = 256, iters = 512;
+  if (bytes < (size_t)blocks * threads * sizeof(double)) return PS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PS_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PS_ECUDA;
+  }
+  poisson_status s = PS_OK;
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && s == PS_OK; ++rep) {   // the first launch warms up
+    cudaEventRecord(e0, st);
+    pp::k_fp64_fma_rate<<<blocks, threads, 0, st>>>((double*)scratch, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      s = PS_ECUDA;
+    else if (rep > 0 && (best == 0.f || ms < best))
+      best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != PS_OK) return s;
+  const double fmas = (double)blocks * threads * iters * 16.0 * 8.0;
+  *gflops = 2.0 * fmas / (best * 1e-3) / 1e9;
+  return PS_OK;
+}

@@ -60,3 +60,13 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_uses_every_core_and_names_the_cpu():
+    """The oracle's all-core timing: one spawned single-threaded process per core, throughput summed."""
+    import bench
+    cb = bench.cpu_baseline(seconds=0.3)
+    assert cb["cores"] == (os.cpu_count() or 1)
+    assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT
+    assert cb["value"] > 0 and cb["single_thread_value"] > 0
+    assert isinstance(cb["cpu"], str) and cb["cpu"]

@@ -262,6 +262,22 @@ def test_fp32_refined_projection_matches_oracle(P, nx, ny, nz, parts, steps, tol
         _native.PS_EINVAL
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-14), (1, 2e-6), (2, 1e-14)])
+def test_divergence_field_matches_oracle(P, prec, tol):
+    """poisson_divergence: f = D(u)/dt of Eq. 7 as a field, element by element."""
+    nx, ny, nz = 48, 20, 36
+    faces = W.tanh_faces(ny, 1.7)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.random_velocity(10, nx, ny, nz)
+    dt = 3e-3
+    want = oracle.divergence(g, u, v, w) / dt
+    plan = P.Plan(nx, ny, nz, faces, precision=prec, pdd_parts=2, device=DEV)
+    dtype = torch.float32 if prec == 1 else torch.float64
+    f = plan.divergence(to_dev(u, dtype), to_dev(v, dtype), to_dev(w, dtype), dt)
+    torch.cuda.synchronize()
+    assert relerr(f.double().cpu().numpy(), want) <= tol
+
+
 def test_bad_arguments_are_rejected(P):
     nx, ny, nz = 8, 8, 8
     plan = P.Plan(nx, ny, nz, W.tanh_faces(ny, 1.5), precision=P.PP_FP64, device=DEV)
