@@ -726,12 +726,19 @@ def batch_form(dev, steps: int = 5, warmup: int = 2, tune: bool = True):
     plans = [P.Plan(c.nx, c.ny, c.nz, sp["y_faces"], precision=P.PP_FP32, device=dev) for c, sp in zip(cases, specs)]
     ms_seq = timed(lambda: [pl.solve(r, out=o) for pl, r, o in zip(plans, rhs, outs)])
     del plans
-    bp = P.BatchPlan(specs, precision=P.PP_FP32, device=dev)
+    bb = P.BatchPlan(specs, precision=P.PP_FP32, device=dev)
+    ms_branches = timed(lambda: bb.solve(rhs, out=outs))
+    branch_kernels = bb.last_launch_count
+    del bb
+    bp = P.BatchPlan(specs, precision=P.PP_FP32, device=dev, persistent=True)
     ms_batch = timed(lambda: bp.solve(rhs, out=outs))
     out = {"workload": "64 uneven FP32 Poisson solves, sizes from default_rng(5)", "points": total,
            "sequential_ms": ms_seq, "sequential_gpts_s": total / (ms_seq * 1e-3) / 1e9,
-           "batched_graph_ms": ms_batch, "batched_graph_gpts_s": total / (ms_batch * 1e-3) / 1e9,
-           "kernels_per_graph_launch": bp.last_launch_count}
+           "graph_branches_ms": ms_branches, "graph_branches_gpts_s": total / (ms_branches * 1e-3) / 1e9,
+           "graph_branches_kernels": branch_kernels,
+           "persistent_ms": ms_batch, "persistent_gpts_s": total / (ms_batch * 1e-3) / 1e9,
+           "persistent_kernels_per_graph_launch": bp.last_launch_count,
+           "persistent_status": bp.device_status()}
     del bp
     if tune:
         t0 = time.perf_counter()

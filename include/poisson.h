@@ -68,11 +68,18 @@ typedef enum {
 #define POISSON_TIMING       0x2u   /* flag: record CUDA events around every kernel launch */
 #define POISSON_GENERIC_FFT  0x4u   /* flag: use the runtime-generic FFT kernels instead of the
                                        compile-time specialised ones (a tiling the autotuner tries) */
+#define POISSON_BATCH_PERSISTENT 0x10u /* batched plans (flag of descs[0]): run the whole batch as ONE
+                                       persistent kernel over a device work queue instead of one
+                                       graph branch per instance (see poisson_solve_batched)      */
 #define POISSON_SELFTEST_WAIT 0x8u  /* diagnostics flag: the x-transform that stages its FP64
                                        input by bulk copies (FP32 plans, Nx/2 >= 256) skips its
                                        first copy, so its bounded wait runs out (~2 s): the call
                                        returns, the result is undefined and the device status
-                                       reads PS_ETIMEOUT.  For testing the failure path only.  */
+                                       reads PS_ETIMEOUT.  For a persistent batched plan (flag of
+                                       descs[0]) the first x-transform item of instance 0 is never
+                                       counted done, so that instance's next waits run out
+                                       (~1 s), the launch aborts and the batch's status word reads
+                                       PS_ETIMEOUT.  For testing the failure path only.          */
 
 typedef struct {
   int nx, ny, nz;           /* cells; nx even, nx/2 and nz of the form 2^a 3^b; ny >= 2 */
@@ -214,10 +221,17 @@ poisson_status poisson_plan_batched(const poisson_desc* descs, int count, poisso
 
 /* Solve every instance i of a batched plan: rhs[i] -> p[i] (host arrays of `count` device
  * pointers, laid out and typed as for poisson_solve).  All instances run in ONE CUDA graph
- * launch on `stream`: each instance's kernel sequence is a branch of the graph, so kernels of
- * different instances run concurrently.  The graph is captured on the first call and replayed
- * while the pointer arrays stay the same (a change of pointers re-captures it).  The first
- * call also runs the batch once outside capture; make it before capturing `stream` yourself. */
+ * launch on `stream`.  By default each instance's kernel sequence is a branch of the graph, so
+ * kernels of different instances run concurrently.  With POISSON_BATCH_PERSISTENT (descs[0].flags)
+ * and every instance a PP_FP32 plan with Nx/2 in {32,48,64,96,128,192}, Nz in
+ * {64,96,128,192,256,384}, ny <= 256 and a warp-scan PDD partition (pdd_parts a power of two <= 32
+ * with ny/pdd_parts in {2,3,4,6,8,12,16}; an automatic partition is chosen so), the graph is ONE
+ * persistent kernel that takes (instance, pass, tiles) work items from a device queue, with
+ * bounded waits (about a second) for the pass each item depends on: a wait that runs out sets
+ * PS_ETIMEOUT in the batch's status word (read by poisson_device_status on the batched plan) and
+ * ends the launch.  The graph is captured on the first call and replayed while the pointer
+ * arrays stay the same (a change of pointers re-captures it).  The first call also runs the batch
+ * once outside capture; make it before capturing `stream` yourself. */
 poisson_status poisson_solve_batched(poisson_plan_t plan, const void* const* rhs, void* const* p, void* stream);
 
 /* Autotuner: for the grid of `desc`, time poisson_solve with every candidate PDD partition

@@ -14,12 +14,12 @@ import torch
 
 from . import _native
 from ._native import (PP_FP64, PP_FP32, PP_FP32_REFINED, PT_AUTO, PT_THOMAS, PT_PDD_EXACT, PT_PDD_TRUNCATED,
-                      POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, POISSON_SELFTEST_WAIT, PoissonError,
-                      check)
+                      POISSON_CHECK_FINITE, POISSON_TIMING, POISSON_GENERIC_FFT, POISSON_SELFTEST_WAIT,
+                      POISSON_BATCH_PERSISTENT, PoissonError, check)
 
 __all__ = ["Plan", "BatchPlan", "autotune", "tune_batch", "fp64_fma_rate", "ProjectionFn", "PoissonError", "POISSON_GENERIC_FFT", "PP_FP64", "PP_FP32", "PP_FP32_REFINED",
            "PT_AUTO", "PT_THOMAS", "PT_PDD_EXACT", "PT_PDD_TRUNCATED", "POISSON_CHECK_FINITE", "POISSON_TIMING",
-           "POISSON_SELFTEST_WAIT"]
+           "POISSON_SELFTEST_WAIT", "POISSON_BATCH_PERSISTENT"]
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -244,13 +244,17 @@ def autotune(nx, ny, nz, y_faces, lx=2 * np.pi, lz=np.pi, precision=PP_FP32, fp6
 
 
 class BatchPlan:
-    """Independent solves of uneven sizes run as one graph launch (poisson_solve_batched).
+    """Independent solves of uneven sizes run as one graph launch (poisson_solve_batched): one graph
+    branch per instance, or with persistent=True one persistent kernel over a device work queue.
 
     specs: sequence of dicts with keys nx, ny, nz, y_faces (and optional lx, lz, pdd_parts,
     flags).  With tune=True each distinct grid is autotuned once (partition count, FFT tiling).
+    selftest_wait=True makes the persistent launch's bounded waits run out (diagnostics:
+    POISSON_SELFTEST_WAIT).
     """
 
-    def __init__(self, specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, tune=False, device=None):
+    def __init__(self, specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, tune=False, device=None,
+                 persistent=False, selftest_wait=False):
         L = _native.lib()
         self.device = torch.device(device if device is not None else "cuda")
         self.precision = int(precision)
@@ -270,6 +274,8 @@ class BatchPlan:
                 parts, flags, _ = cache[key]
             self.tuned.append((parts, flags))
             tri = PT_THOMAS if parts == 1 else (PT_PDD_EXACT if parts > 1 else PT_AUTO)
+            if i == 0:
+                flags |= (POISSON_BATCH_PERSISTENT if persistent else 0) | (POISSON_SELFTEST_WAIT if selftest_wait else 0)
             d, faces = _desc(s["nx"], s["ny"], s["nz"], s["y_faces"], lx, lz, precision, tri, parts, fp64_low_modes,
                              refine_steps, flags)
             descs[i] = d
@@ -309,6 +315,10 @@ class BatchPlan:
     def last_launch_count(self) -> int:
         return int(_native.lib().poisson_last_launch_count(self._h))
 
+    def device_status(self, stream=None) -> int:
+        """Synchronise and read (then clear) the batch's status word (PS_ETIMEOUT after a wait ran out)."""
+        return int(_native.lib().poisson_device_status(self._h, _stream(stream)))
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and _native._LIB is not None:
@@ -324,10 +334,21 @@ def _max_parts(ny):
     return best
 
 
+def _scan_parts(ny, mmax):
+    """The smallest power-of-two partition P <= 32 whose blocks (ny / P rows, one of the heights of
+    the warp-scan PDD tiles) have at most mmax rows, else 0."""
+    for P in (1, 2, 4, 8, 16, 32):
+        if ny % P == 0 and ny // P <= mmax and ny // P in (1, 2, 3, 4, 6, 8, 12, 16, 24):
+            return P
+    return 0
+
+
 def tune_batch(specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, device=None, repeats=3):
-    """Batch-level autotuner: time whole batched graph launches for several partition strategies
-    (the plan's model, per-shape autotuning, Thomas everywhere, the largest partition count) on
-    the device and return (best BatchPlan, {strategy: ms})."""
+    """Batch-level autotuner: time whole batched graph launches on the device for several strategies
+    and return (best BatchPlan, {strategy: ms}).  Strategies: one graph branch per instance with the
+    plan's partition model, with per-shape autotuning (poisson_autotune: partition count and FFT
+    tiling), with Thomas everywhere, with the largest partition count; and the persistent
+    work-queue launch with blocks of at most 16 or at most 8 rows."""
     dev = torch.device(device if device is not None else "cuda")
     dtype = torch.float32 if precision == PP_FP32 else torch.float64
     gen = torch.Generator(device=dev)
@@ -338,11 +359,15 @@ def tune_batch(specs, precision=PP_FP32, fp64_low_modes=4, refine_steps=1, devic
         "model": [dict(s) for s in specs],
         "thomas": [dict(s, pdd_parts=1) for s in specs],
         "max_parts": [dict(s, pdd_parts=_max_parts(s["ny"])) for s in specs],
+        "persistent": [dict(s) for s in specs],
+        "persistent_m8": [dict(s, pdd_parts=_scan_parts(s["ny"], 8)) for s in specs],
     }
     times, best, best_ms = {}, None, None
-    for name in ("model", "per_shape", "thomas", "max_parts"):
+    for name in ("model", "per_shape", "thomas", "max_parts", "persistent", "persistent_m8"):
+        if name == "persistent_m8" and (precision != PP_FP32 or any(s["pdd_parts"] == 0 for s in strategies[name])):
+            continue
         bp = BatchPlan(specs if name == "per_shape" else strategies[name], precision, fp64_low_modes, refine_steps,
-                       tune=(name == "per_shape"), device=dev)
+                       tune=(name == "per_shape"), device=dev, persistent=name.startswith("persistent"))
         bp.solve(rhs, out=outs)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

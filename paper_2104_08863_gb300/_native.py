@@ -20,6 +20,7 @@ POISSON_CHECK_FINITE = 0x1
 POISSON_TIMING = 0x2
 POISSON_GENERIC_FFT = 0x4
 POISSON_SELFTEST_WAIT = 0x8
+POISSON_BATCH_PERSISTENT = 0x10
 
 # Every symbol declared in include/poisson.h.
 EXPORTS = (

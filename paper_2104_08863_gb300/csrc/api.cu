@@ -922,7 +922,7 @@ poisson_status poisson_plan_set_chain(poisson_plan_t pl, int slab_cols, int stre
 
 poisson_status poisson_device_status(poisson_plan_t pl, void* stream) {
   if (!pl) return PS_EINVAL;
-  if (!pl->ws) return PS_ENOWORKSPACE;
+  if (!pl->ws || !pl->dt.status) return PS_ENOWORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   int h = 0;
   if (cudaMemcpyAsync(&h, pl->dt.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;

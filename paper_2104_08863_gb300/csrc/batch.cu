@@ -1,10 +1,12 @@
 // Batched solves of independent, uneven-size problems in one graph launch, and the autotuner.
 //
 // A batched plan holds one sub-plan per instance and carves their workspaces out of one caller
-// allocation.  poisson_solve_batched captures, once, a CUDA graph in which every instance's
-// kernel sequence (the same pipeline as poisson_solve) is a branch forked from the caller's
-// stream, so that small instances run concurrently and the host pays one graph launch per
-// batch instead of ~7 launches per instance; later calls with the same pointers replay it.
+// allocation.  poisson_solve_batched captures, once, a CUDA graph and replays it while the
+// pointers stay the same.  The graph holds either one branch per instance, forked from the
+// caller's stream and holding that instance's kernel sequence (the same pipeline as
+// poisson_solve), so that small instances run concurrently and the host pays one graph launch
+// per batch instead of ~7 launches per instance; or (POISSON_BATCH_PERSISTENT, every instance
+// supported) one persistent kernel over a device work list (batch_persistent.cu).
 //
 // poisson_autotune picks, per grid, the PDD partition count and the FFT tiling (compile-time
 // specialised or generic kernels) by timing the actual solve on the device.
@@ -14,6 +16,7 @@
 #include <new>
 #include <vector>
 
+#include "batch_persistent.h"
 #include "internal.h"
 
 namespace {
@@ -31,6 +34,53 @@ void drop_graph(poisson_plan_s* pl) {
 
 namespace pp {
 
+// Instance table and work list of the persistent launch, built once per workspace.  Items are
+// ordered pass by pass; within a pass the instances go largest first.
+static poisson_status build_persistent(poisson_plan_s* pl, unsigned char* ws, cudaStream_t st) {
+  const int n = (int)pl->children.size();
+  std::vector<BatchInst> inst(n);
+  std::vector<int> order(n);
+  size_t lowoff = pl->off_lowscr;
+  for (int i = 0; i < n; ++i) {
+    poisson_plan_s* c = pl->children[i];
+    BatchInst& b = inst[i];
+    memset(&b, 0, sizeof(b));
+    b.g = c->g;
+    b.dt = c->dt;
+    b.spec = (cplx<float>*)(c->ws + c->off_spec);
+    b.parts = c->parts;
+    b.low = c->low;
+    if (!batch_persistent_ok(c, b.xsel, b.zsel, b.msel)) return PS_EUNSUPPORTED;
+    b.zcols = batch_zcols(c);
+    batch_tiles(c, b.zcols, b.ntiles);
+    const size_t nlow = c->low >= 0 ? (size_t)(c->low + 1) * (2 * c->low + 1) : 0;
+    b.low_piv = (double*)(ws + lowoff);
+    lowoff = align256(lowoff + 8 * nlow * c->g.ny);
+    b.low_y = (cplx<double>*)(ws + lowoff);
+    lowoff = align256(lowoff + 16 * nlow * c->g.ny);
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const size_t px = (size_t)inst[x].g.nx * inst[x].g.ny * inst[x].g.nz;
+    const size_t py = (size_t)inst[y].g.nx * inst[y].g.ny * inst[y].g.nz;
+    return px > py;
+  });
+  std::vector<BatchItem> items;
+  for (int pass = 0; pass < BP_N; ++pass)
+    for (int i : order) {
+      const int grp = batch_group(pl->children[i], pass, inst[i].zcols);
+      for (int t = 0; t < inst[i].ntiles[pass]; t += grp)
+        items.push_back(BatchItem{i, pass, t, std::min(grp, inst[i].ntiles[pass] - t)});
+    }
+  pl->nitems = (int)items.size();
+  pl->inst_host.assign((unsigned char*)inst.data(), (unsigned char*)inst.data() + n * sizeof(BatchInst));
+  if (cudaMemcpyAsync(ws + pl->off_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return PS_ECUDA;
+  if (cudaMemsetAsync(ws + pl->off_bstatus, 0, 256, st) != cudaSuccess) return PS_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? PS_OK : PS_ECUDA;
+}
+
 poisson_status set_batch_workspace(poisson_plan_s* pl, unsigned char* ws, void* stream) {
   size_t off = 0;
   for (poisson_plan_s* c : pl->children) {
@@ -39,9 +89,13 @@ poisson_status set_batch_workspace(poisson_plan_s* pl, unsigned char* ws, void* 
     off += align256(c->ws_bytes);
   }
   pl->ws = ws;
+  pl->dt = DevTables{};
+  pl->dt.status = (int*)(ws + pl->off_bstatus);
   drop_graph(pl);
   pl->warmed = false;
-  return PS_OK;
+  if (cudaMemsetAsync(ws + pl->off_bstatus, 0, 256, (cudaStream_t)stream) != cudaSuccess) return PS_ECUDA;
+  if (pl->persistent) return build_persistent(pl, ws, (cudaStream_t)stream);
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? PS_OK : PS_ECUDA;
 }
 
 void destroy_batch(poisson_plan_s* pl) {
@@ -62,9 +116,21 @@ poisson_status poisson_plan_batched(const poisson_desc* descs, int count, poisso
   poisson_plan_s* pl = new (std::nothrow) poisson_plan_s();
   if (!pl) return PS_ENOMEM;
   size_t total = 0;
+  const bool branches = (descs[0].flags & POISSON_BATCH_PERSISTENT) == 0;
   for (int i = 0; i < count; ++i) {
+    poisson_desc d = descs[i];
+    // the persistent launch's PDD tiles take blocks of at most 16 rows (register budget): an
+    // automatic partition becomes the smallest power of two P <= 32 with ny / P <= 16
+    if (!branches && d.precision == PP_FP32 && d.pdd_parts == 0 && d.tridiag == PT_AUTO) {
+      for (int P = 1; P <= 32; P *= 2)
+        if (d.ny % P == 0 && d.ny / P <= 16 && pp::reg_tridiag_ok(d.ny, P)) {
+          d.pdd_parts = P;
+          d.tridiag = P == 1 ? PT_THOMAS : PT_PDD_EXACT;
+          break;
+        }
+    }
     poisson_plan_t c = nullptr;
-    const poisson_status s = poisson_plan_create(&descs[i], &c);
+    const poisson_status s = poisson_plan_create(&d, &c);
     if (s != PS_OK) {
       pp::destroy_batch(pl);
       delete pl;
@@ -72,6 +138,38 @@ poisson_status poisson_plan_batched(const poisson_desc* descs, int count, poisso
     }
     pl->children.push_back(c);
     total += align256(c->ws_bytes);
+  }
+  // the batch's own regions after the instances' workspaces: status word, then (persistent
+  // launch) the instance table, the work list, the control block and the low modes' scratch
+  pl->off_bstatus = total;
+  total += 256;
+  bool ok = !branches;
+  size_t nitems = 0, lowscr = 0;
+  for (int i = 0; ok && i < count; ++i) {
+    poisson_plan_s* c = pl->children[i];
+    int xs, zs, ms;
+    if (!pp::batch_persistent_ok(c, xs, zs, ms)) {
+      ok = false;
+      break;
+    }
+    int nt[pp::BP_N];
+    pp::batch_tiles(c, pp::batch_zcols(c), nt);
+    for (int k = 0; k < pp::BP_N; ++k) nitems += (size_t)nt[k];
+    const size_t nlow = c->low >= 0 ? (size_t)(c->low + 1) * (2 * c->low + 1) : 0;
+    lowscr += align256(8 * nlow * c->g.ny) + align256(16 * nlow * c->g.ny);
+  }
+  if (ok && nitems < (size_t)1 << 30) {
+    pl->persistent = true;
+    pl->selftest = (descs[0].flags & POISSON_SELFTEST_WAIT) != 0;
+    pl->off_inst = total;
+    total += align256((size_t)count * sizeof(pp::BatchInst));
+    pl->off_items = total;
+    total += align256(nitems * sizeof(pp::BatchItem));
+    pl->off_ctl = total;
+    pl->ctl_bytes = sizeof(pp::BatchCtl) + sizeof(unsigned) * ((size_t)count * pp::BP_N);
+    total += align256(pl->ctl_bytes);
+    pl->off_lowscr = total;
+    total += lowscr;
   }
   pl->ws_bytes = total;
   pl->ws = nullptr;
@@ -93,6 +191,55 @@ poisson_status poisson_solve_batched(poisson_plan_t pl, const void* const* rhs, 
   cudaStream_t st = (cudaStream_t)stream;
   bool same = pl->gexec && (int)pl->g_rhs.size() == n;
   for (int i = 0; same && i < n; ++i) same = pl->g_rhs[i] == rhs[i] && pl->g_p[i] == p[i];
+  if (pl->persistent) {
+    if (!same) {
+      drop_graph(pl);
+      if (pl->forks.empty()) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PS_ECUDA;
+        pl->forks.push_back(s);
+      }
+      pp::BatchInst* inst = (pp::BatchInst*)pl->inst_host.data();
+      for (int i = 0; i < n; ++i) {
+        inst[i].rhs = (const float*)rhs[i];
+        inst[i].out = (float*)p[i];
+      }
+      unsigned char* ws = pl->ws;
+      if (cudaMemcpyAsync(ws + pl->off_inst, pl->inst_host.data(), pl->inst_host.size(), cudaMemcpyHostToDevice,
+                          st) != cudaSuccess)
+        return PS_ECUDA;
+      auto launch = [&](cudaStream_t s) {
+        return pp::launch_batch_persistent((const pp::BatchInst*)(ws + pl->off_inst),
+                                           (const pp::BatchItem*)(ws + pl->off_items), pl->nitems,
+                                           (pp::BatchCtl*)(ws + pl->off_ctl), pl->ctl_bytes,
+                                           (int*)(ws + pl->off_bstatus), pl->selftest ? 1 : 0, s);
+      };
+      if (!pl->warmed) {   // one plain launch: kernel attributes and the grid size are set outside capture
+        if (launch(st) != cudaSuccess) return PS_ECUDA;
+        pl->warmed = true;
+      }
+      if (cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+      cudaStream_t cap = pl->forks[0];
+      if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PS_ECUDA;
+      const cudaError_t el = launch(cap);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+      if (el != cudaSuccess || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return PS_ECUDA;
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        pl->gexec = nullptr;
+        return PS_ECUDA;
+      }
+      pl->g_rhs.assign(rhs, rhs + n);
+      pl->g_p.assign(p, p + n);
+    }
+    pl->launches = 1;
+    return cudaGraphLaunch(pl->gexec, st) == cudaSuccess ? PS_OK : PS_ECUDA;
+  }
   if (!same) {
     drop_graph(pl);
     while ((int)pl->forks.size() < n + 1) {   // n branches + the capture stream

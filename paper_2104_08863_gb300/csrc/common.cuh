@@ -37,6 +37,13 @@ template <typename T> __device__ __forceinline__ cplx<T> ld_c(const cplx<T>* p) 
   typename vec2<T>::type v = *reinterpret_cast<const typename vec2<T>::type*>(p);
   return mk<T>(v.x, v.y);
 }
+// A load that is coherent with stores made by other CTAs earlier in the same launch (through L2;
+// never the read-only path).
+template <typename T> __device__ __forceinline__ cplx<T> ld_c_cg(const cplx<T>* p) {
+  const typename vec2<T>::type v = __ldcg(reinterpret_cast<const typename vec2<T>::type*>(p));
+  return mk<T>(v.x, v.y);
+}
+
 template <typename T> __device__ __forceinline__ void st_c(cplx<T>* p, cplx<T> a) {
   typename vec2<T>::type v; v.x = a.x; v.y = a.y;
   *reinterpret_cast<typename vec2<T>::type*>(p) = v;

@@ -148,18 +148,18 @@ cudaError_t launch_tridiag_factored_f32(const Geometry& g, const DevTables& tb, 
 // FP32 PDD with each block of m = ny/P rows held in one thread's registers and its factors
 // computed on the fly (no factor tables): m in {1, 2, 3, 4, 6, 8, 12, 16, 24}, P <= 256, S = 256/P
 // systems per CTA (at least 1).  Other (ny, P) use the factored kernel with tables.
-inline bool reg_tridiag_ok(int ny, int P) {
+__host__ __device__ inline bool reg_tridiag_ok(int ny, int P) {
   if (P < 1 || P > 256 || ny % P) return false;
   const int m = ny / P;
   return m == 1 || m == 2 || m == 3 || m == 4 || m == 6 || m == 8 || m == 12 || m == 16 || m == 24;
 }
-inline int reg_systems_per_cta(int P) { return P >= 256 ? 1 : 256 / P; }
+__host__ __device__ inline int reg_systems_per_cta(int P) { return P >= 256 ? 1 : 256 / P; }
 // [kx_lo, kx_hi): the kx columns solved (kx_hi < 0: all); a partial range is supported by the
 // warp-scan variant only (P a power of two <= 32), with kx_lo a multiple of
 // reg_systems_per_cta(P), and is refused (cudaErrorNotSupported) otherwise.
 cudaError_t launch_tridiag_reg_f32(const Geometry& g, const DevTables& tb, int parts, int low_modes,
                                    cplx<float>* spec, cudaStream_t st, int kx_lo = 0, int kx_hi = -1);
-inline bool scan_tridiag_ok(int ny, int P) { return reg_tridiag_ok(ny, P) && P <= 32 && (P & (P - 1)) == 0; }
+__host__ __device__ inline bool scan_tridiag_ok(int ny, int P) { return reg_tridiag_ok(ny, P) && P <= 32 && (P & (P - 1)) == 0; }
 // Bytes of the reduced-system table of the register kernel, and its FP64 set-up (once per plan).
 size_t reduced_table_bytes(const Geometry& g, int parts);
 cudaError_t launch_reduced_setup(const Geometry& g, const DevTables& tb, int parts, bool trunc, float* tab,
@@ -266,6 +266,13 @@ struct poisson_plan_s {
   std::vector<const void*> g_rhs;
   std::vector<void*> g_p;
   bool warmed = false;
+  // persistent batched launch (batch_persistent.cu): on when POISSON_BATCH_PERSISTENT is set and
+  // every instance is supported; byte offsets of its regions after the instances' workspaces
+  bool persistent = false;
+  bool selftest = false;
+  size_t off_bstatus = 0, off_inst = 0, off_items = 0, off_ctl = 0, ctl_bytes = 0, off_lowscr = 0;
+  int nitems = 0;
+  std::vector<unsigned char> inst_host;   // host image of the instance table
 };
 
 namespace pp {

@@ -34,16 +34,18 @@ template <int M> struct XReg {
 
 // Forward x-transform of an FP32 field into the FP32 half spectrum; MODE as in fwd_load
 // (FWD_PLAIN, FWD_DIV, FWD_GRADT).
+// One tile: lines tile * LPB .. + LPB - 1.  Called by every thread of the CTA (blockDim.x >=
+// C::THREADS; threads past C::THREADS only take part in the barriers).
 template <typename TI, int M, int MODE>
-__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
-    k_fwd_x_reg(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
-                int nlines) {
+__device__ __forceinline__ void fwd_x_reg_tile(const Geometry& g, const FwdArgs& args, const Tables<float>& tt,
+                                               const DevTables& tb, cplx<float>* __restrict__ spec, int nlines,
+                                               int tile, unsigned char* smem_raw) {
   using C = XReg<M>;
   constexpr int N1 = C::N1, N2 = C::N2, LPB = C::LPB, B = C::B, LS = C::LS, THREADS = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);
-  const int line0 = blockIdx.x * LPB;
-  {
+  const int line0 = tile * LPB;
+  const bool live = threadIdx.x < THREADS;
+  if (live) {
     const int t = threadIdx.x / N1, n1 = threadIdx.x - t * N1;
     const int line = line0 + t;
     cplx<float> v[N2];
@@ -84,30 +86,41 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 2)
   }
   __syncthreads();
   constexpr int M1 = M + 1;
+  if (live) {
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
-    const int t = idx / M1, kx = idx - t * M1;
-    const int line = line0 + t;
-    if (line >= nlines) continue;
-    const cplx<float>* nat = buf + t * LS;
-    const cplx<float> Zk = nat[kx == M ? 0 : kx];
-    const cplx<float> Zc = conj(nat[kx == 0 ? 0 : M - kx]);
-    st_c(spec + (size_t)line * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+    for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
+      const int t = idx / M1, kx = idx - t * M1;
+      const int line = line0 + t;
+      if (line >= nlines) continue;
+      const cplx<float>* nat = buf + t * LS;
+      const cplx<float> Zk = nat[kx == M ? 0 : kx];
+      const cplx<float> Zc = conj(nat[kx == 0 ? 0 : M - kx]);
+      st_c(spec + (size_t)line * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+    }
   }
+}
+
+template <typename TI, int M, int MODE>
+__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+    k_fwd_x_reg(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
+                int nlines) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fwd_x_reg_tile<TI, M, MODE>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
 }
 
 // Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE
 // (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1].
 template <typename TO, int M, int MODE, bool ACC>
-__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
-    k_inv_x_reg(Geometry g, Tables<float> tt, const cplx<float>* __restrict__ spec, TO* __restrict__ out, double scl,
-                int nlines, const double* __restrict__ dy, double* __restrict__ acc, PairArgs pair) {
+__device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<float>& tt,
+                                               const cplx<float>* __restrict__ spec, TO* __restrict__ out,
+                                               double scl, int nlines, const double* __restrict__ dy,
+                                               double* __restrict__ acc, const PairArgs& pair, int tile,
+                                               unsigned char* smem_raw) {
   using C = XReg<M>;
   constexpr int N1 = C::N1, N2 = C::N2, LPB = C::LPB, B = C::B, LS = C::LS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);
-  const int line0 = blockIdx.x * LPB;
-  {
+  const int line0 = tile * LPB;
+  if (threadIdx.x < C::THREADS) {
     const int t = threadIdx.x / N1, n1 = threadIdx.x - t * N1;
     const int line = line0 + t;
     cplx<float> v[N2];
@@ -117,8 +130,8 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 2)
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
         const int n = n1 + N1 * n2;
-        xk[n2] = ld_c(X + n);
-        xm[n2] = ld_c(X + (M - n));
+        xk[n2] = ld_c_cg(X + n);   // coherent with a persistent launch's earlier stores
+        xm[n2] = ld_c_cg(X + (M - n));
       }
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
@@ -171,6 +184,14 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 2)
     for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
     if ((threadIdx.x & 31) == 0 && wsum != 0.0) atomicAdd(acc + 1, wsum);
   }
+}
+
+template <typename TO, int M, int MODE, bool ACC>
+__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+    k_inv_x_reg(Geometry g, Tables<float> tt, const cplx<float>* __restrict__ spec, TO* __restrict__ out, double scl,
+                int nlines, const double* __restrict__ dy, double* __restrict__ acc, PairArgs pair) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  inv_x_reg_tile<TO, M, MODE, ACC>(g, tt, spec, out, scl, nlines, dy, acc, pair, blockIdx.x, smem_raw);
 }
 
 }  // namespace pp
