@@ -186,8 +186,11 @@ __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<f
   }
 }
 
+// Three CTAs per SM (85 registers): the inverse's pass 2 streams its results straight from
+// registers, and the extra resident warps hide that more than the spills it causes cost (1.9 vs
+// 2.1 ms per pass at 1536x768x1024; the forward and the z-transform measured the other way).
 template <typename TO, int M, int MODE, bool ACC>
-__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+__global__ void __launch_bounds__(XReg<M>::THREADS, 3)
     k_inv_x_reg(Geometry g, Tables<float> tt, const cplx<float>* __restrict__ spec, TO* __restrict__ out, double scl,
                 int nlines, const double* __restrict__ dy, double* __restrict__ acc, PairArgs pair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
