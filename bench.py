@@ -833,6 +833,8 @@ PROFILE_CASES = {
                                         "solve"),
     # the precision form itself (launch lists only: one metric pass)
     "fp32_refined_solve_1536x768x1024": (W.CHANNEL_1536, 2, 1, "solve"),
+    # the 64 uneven FP32 solves of the batched form as one persistent work-queue launch
+    "batch64_persistent": (None, 1, 0, "batch"),
 }
 
 
@@ -845,6 +847,19 @@ def profile_case(name: str, repeats: int = 2):
     case, prec, steps, kind = PROFILE_CASES[name][:4]
     extra = PROFILE_CASES[name][4] if len(PROFILE_CASES[name]) > 4 else 0
     dev = torch.device("cuda", 0)
+    if kind == "batch":
+        cases = W.batch_instances(5, 64)
+        specs = [dict(nx=c.nx, ny=c.ny, nz=c.nz, y_faces=W.tanh_faces(c.ny, c.stretch)) for c in cases]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5)
+        rhs = [torch.randn(c.ny, c.nz, c.nx, dtype=torch.float32, device=dev, generator=gen) for c in cases]
+        bp = P.BatchPlan(specs, precision=P.PP_FP32, device=dev, persistent=True)
+        outs = [torch.empty_like(r) for r in rhs]
+        for _ in range(repeats):
+            bp.solve(rhs, out=outs)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": name, "launches_per_call": bp.last_launch_count}))
+        return
     faces = W.tanh_faces(case.ny, case.stretch)
     parts = PDD_PARTS if (prec == P.PP_FP64 and case.ny % PDD_PARTS == 0) else 0
     plan = P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec, pdd_parts=parts,
