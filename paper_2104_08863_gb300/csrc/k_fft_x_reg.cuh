@@ -100,8 +100,9 @@ __device__ __forceinline__ void fwd_x_reg_tile(const Geometry& g, const FwdArgs&
   }
 }
 
+// Three CTAs per SM (85 registers), as for the inverse below.
 template <typename TI, int M, int MODE>
-__global__ void __launch_bounds__(XReg<M>::THREADS, 2)
+__global__ void __launch_bounds__(XReg<M>::THREADS, 3)
     k_fwd_x_reg(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
                 int nlines) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
