@@ -12,6 +12,7 @@
 #include <mutex>
 #include <utility>
 
+#include "bulk_copy.cuh"
 #include "fft_static.cuh"
 #include "k_fft_x_reg.cuh"
 #include "xline.cuh"
@@ -198,41 +199,6 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
 // staging area directly (packing or converting on the way), after which the copy of the next tile
 // is issued, so it travels while this tile is transformed and stored.  The arithmetic is that of
 // the single-tile kernels above.
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Thread 0: `bytes` (a multiple of 16; both addresses 16-byte aligned) from gmem to smem, counted
-// on bar.  The proxy fence orders the CTA's earlier generic reads of the destination (made
-// visible to thread 0 by a barrier) before the asynchronous write.
-__device__ __forceinline__ void bulk_load(void* smem, const void* gmem, unsigned bytes, uint64_t* bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(smem)),
-               "l"(gmem), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-// Bounded wait for the completion of phase `parity` of bar; false after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  const long long t0 = clock64();
-  for (unsigned it = 0; it < (1u << 26); ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > (1LL << 32)) return false;
-  }
-  return false;
-}
 
 template <typename TI, int M> struct XPipe {
   using X = XTile<float, M>;

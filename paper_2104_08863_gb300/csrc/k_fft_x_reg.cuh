@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 3)
 }
 
 // Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE
-// (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1].
+// (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1], formed in double-float arithmetic on the
+// FP32 units (one FP64 atomic per warp).
 template <typename TO, int M, int MODE, bool ACC>
 __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<float>& tt,
                                                const cplx<float>* __restrict__ spec, TO* __restrict__ out,
@@ -158,7 +159,7 @@ __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<f
   const int t2 = threadIdx.x / N2, k2 = threadIdx.x - t2 * N2;
   const int line = line0 + t2;
   const bool act = threadIdx.x < P2 && line < nlines;
-  double wsum = 0.0;
+  df w{0.f, 0.f};   // this thread's dy-weighted sum as a double-float
   if (act) {
     cplx<float> u[N1];
     const cplx<float>* row = buf + t2 * LS + k2 * B;
@@ -166,24 +167,44 @@ __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<f
     for (int n1 = 0; n1 < N1; ++n1) u[n1] = row[n1];
     reg_dft<float, N1, 1>(u);
     const float s = float(scl);
-    TO* o = out + (size_t)line * g.nx + 2 * k2;
-    float hs = 0.f, hc = 0.f;
+    const size_t o0 = (size_t)line * g.nx + 2 * k2;
+    // compensated sums of the even and the odd outputs, two independent chains per lane
+    float2 hs[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 hc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     static_for<0, N1>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
       constexpr int k1 = reg_freq(N1, sl);
       const float x0 = u[sl].x * s, x1 = u[sl].y * s;
-      inv_store<float, TO, MODE>(o + 2 * N2 * k1, 0, x0, x1, pair);
+      inv_store<float, TO, MODE>(out + o0 + 2 * N2 * k1, o0 + 2 * N2 * k1, x0, x1, pair);
       if constexpr (ACC) {
-        acc_add(hs, hc, x0);
-        acc_add(hs, hc, x1);
+        const df2 t = two_sum2(hs[sl & 1], make_float2(x0, x1));
+        hs[sl & 1] = t.hi;
+        hc[sl & 1] = f2add(hc[sl & 1], t.lo);
       }
     });
-    if constexpr (ACC) wsum = dy[line / g.nz] * ((double)hs + (double)hc);
+    if constexpr (ACC) {
+      // the four partial sums, then times dy_j split into two floats (TwoProd by FMA)
+      df a = two_sum_df(hs[0].x, hs[0].y), b = two_sum_df(hs[1].x, hs[1].y);
+      a.lo += (hc[0].x + hc[0].y);
+      b.lo += (hc[1].x + hc[1].y);
+      const df sum = df_add(a, b);
+      float dh, dl;
+      f64_split(dy[line / g.nz], dh, dl);
+      const float ph = sum.hi * dh;
+      w = df{ph, fmaf(sum.hi, dh, -ph) + (sum.hi * dl + sum.lo * dh)};
+    }
   }
   if constexpr (ACC) {
+    // warp sum in double-float, one FP64 atomic per warp
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    if ((threadIdx.x & 31) == 0 && wsum != 0.0) atomicAdd(acc + 1, wsum);
+    for (int o = 16; o > 0; o >>= 1) {
+      const df y{__shfl_xor_sync(0xffffffffu, w.hi, o), __shfl_xor_sync(0xffffffffu, w.lo, o)};
+      w = df_add(w, y);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      const double wsum = (double)w.hi + (double)w.lo;
+      if (wsum != 0.0) atomicAdd(acc + 1, wsum);
+    }
   }
 }
 

@@ -72,64 +72,19 @@ __device__ __forceinline__ float2 shfl_down2(float2 v, int d) {
   return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
 }
 
-// One tile of S systems (tile = kz * ntile + kx tile, ntile tiles over [kx_lo, kx_hi)); P * S
-// threads (256 with S = 256/P); `smem` holds the staged rows and the coefficient copies.
+// The sweeps of one system's block and the reduced interface system, on a staged tile: thread
+// (s, b) with `blk` its block's first row (row i at blk[i * S], updated in place), `ab`, `cb` the
+// block's a and c (a_{bM+i} at ab[i]); `active` false for the (0, 0) mode, the FP64 low modes
+// and columns outside the launch, which take part in the shuffles only; (vL, inv, X01, X10, tw)
+// the record of interface b of the system's reduced LU (b < P-1).
 template <int M>
-__device__ __forceinline__ void tridiag_scan_tile(const Geometry& g, int P, int S, int low, const float* __restrict__ a,
-                                                  const float* __restrict__ c, const double* __restrict__ lamx,
-                                                  const double* __restrict__ lamz, const float* __restrict__ rtab,
-                                                  cplx<float>* __restrict__ spec, int kx_lo, int kx_hi, int tile_id,
-                                                  unsigned char* smem) {
-  float2* tile = reinterpret_cast<float2*>(smem);   // [b][i][s] with block stride BS, then a and c
-  const int NT = P * S;
-  const int BS = M * S + 1;
-  constexpr int MS = M | 1;                        // odd per-block stride of the coefficient copies
-  float* as = reinterpret_cast<float*>(tile + (size_t)P * BS);
-  float* csm = as + P * MS;
-  for (int j = threadIdx.x; j < g.ny; j += NT) {
-    const int bj = j / M, ij = j - bj * M;
-    as[bj * MS + ij] = a[j];
-    csm[bj * MS + ij] = c[j];
-  }
-  // a CTA owns the S systems kx0 .. kx0+S-1 of one kz, within the launch's columns
-  // [kx_lo, kx_hi) (kx_lo a multiple of S); columns past the padded row (pitch) are not touched,
-  // columns in [ncols, pitch) are padding and go back unchanged (the last slab copies them)
-  const int ntile = (kx_hi - kx_lo + S - 1) / S;
-  const int kz = tile_id / ntile;
-  const int kx0 = kx_lo + (tile_id - kz * ntile) * S;
-  const int copy_hi = kx_hi >= g.ncols ? g.pitch : kx_hi;
-  const size_t rstride = (size_t)g.nz * g.pitch;
-  // ---- coalesced copy-in: thread t copies block t / S of system t % S (S-system row segments)
-  const int cpb = threadIdx.x / S, cps = threadIdx.x - cpb * S;
-  const bool cvalid = kx0 + cps < copy_hi;
-  const float2* gsrc = reinterpret_cast<const float2*>(spec) + (size_t)kz * g.pitch + kx0 + cps +
-                       (size_t)cpb * M * rstride;
-  float2* tsrc = tile + cpb * BS + cps;
-  if (cvalid) {
-#pragma unroll
-    for (int i = 0; i < M; ++i) cp_async8(tsrc + i * S, gsrc + (size_t)i * rstride);
-  }
-  // ---- compute role: thread (s, b); its interface record is fetched while the tile lands
-  const int s = threadIdx.x / P, b = threadIdx.x - s * P;
+__device__ __forceinline__ void scan_sweeps(int P, int S, float2* blk, const float* ab, const float* cb, int b,
+                                            bool active, float sigma, float vL, float inv, float X01, float X10,
+                                            float tw) {
   const int lseg = b;
-  const int kx = kx0 + s;
-  const int sys = kz * g.ncols + kx;
-  const bool active = kx < kx_hi && kx < g.ncols && !(kx == 0 && kz == 0) && !is_low(kx, kz, g.nz, low);
-  float vL = 0.f, inv = 0.f, X01 = 0.f, X10 = 0.f, tw = 0.f;
-  if (P > 1 && active && b < P - 1) {
-    const float* t = rtab + ((size_t)sys * (P - 1) + b) * 5;
-    vL = __ldg(t); inv = __ldg(t + 1); X01 = __ldg(t + 2); X10 = __ldg(t + 3); tw = __ldg(t + 4);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  const int r0 = b * M;
-  float2* blk = tile + b * BS + s;   // row i at blk[i * S]
-  const float* ab = as + b * MS;      // a_{r0 + i} at ab[i]
-  const float* cb = csm + b * MS;
   float rbv[M], gvv[M];
   float2 xF = make_float2(0.f, 0.f), xL = make_float2(0.f, 0.f);
   if (active) {
-    const float sigma = float(-(lamx[kx] + lamz[kz]));
     float e = ab[0] + sigma, gv = ab[0], rb = rcp_nr(cb[0] + e);
     float run = 1.f;
     float2 gg = make_float2(0.f, 0.f);
@@ -190,6 +145,59 @@ __device__ __forceinline__ void tridiag_scan_tile(const Geometry& g, int P, int 
       blk[i * S] = xn;
     }
   }
+}
+
+// One tile of S systems (tile = kz * ntile + kx tile, ntile tiles over [kx_lo, kx_hi)); P * S
+// threads (256 with S = 256/P); `smem` holds the staged rows and the coefficient copies.
+template <int M>
+__device__ __forceinline__ void tridiag_scan_tile(const Geometry& g, int P, int S, int low, const float* __restrict__ a,
+                                                  const float* __restrict__ c, const double* __restrict__ lamx,
+                                                  const double* __restrict__ lamz, const float* __restrict__ rtab,
+                                                  cplx<float>* __restrict__ spec, int kx_lo, int kx_hi, int tile_id,
+                                                  unsigned char* smem) {
+  float2* tile = reinterpret_cast<float2*>(smem);   // [b][i][s] with block stride BS, then a and c
+  const int NT = P * S;
+  const int BS = M * S + 1;
+  constexpr int MS = M | 1;                        // odd per-block stride of the coefficient copies
+  float* as = reinterpret_cast<float*>(tile + (size_t)P * BS);
+  float* csm = as + P * MS;
+  for (int j = threadIdx.x; j < g.ny; j += NT) {
+    const int bj = j / M, ij = j - bj * M;
+    as[bj * MS + ij] = a[j];
+    csm[bj * MS + ij] = c[j];
+  }
+  // a CTA owns the S systems kx0 .. kx0+S-1 of one kz, within the launch's columns
+  // [kx_lo, kx_hi) (kx_lo a multiple of S); columns past the padded row (pitch) are not touched,
+  // columns in [ncols, pitch) are padding and go back unchanged (the last slab copies them)
+  const int ntile = (kx_hi - kx_lo + S - 1) / S;
+  const int kz = tile_id / ntile;
+  const int kx0 = kx_lo + (tile_id - kz * ntile) * S;
+  const int copy_hi = kx_hi >= g.ncols ? g.pitch : kx_hi;
+  const size_t rstride = (size_t)g.nz * g.pitch;
+  // ---- coalesced copy-in: thread t copies block t / S of system t % S (S-system row segments)
+  const int cpb = threadIdx.x / S, cps = threadIdx.x - cpb * S;
+  const bool cvalid = kx0 + cps < copy_hi;
+  const float2* gsrc = reinterpret_cast<const float2*>(spec) + (size_t)kz * g.pitch + kx0 + cps +
+                       (size_t)cpb * M * rstride;
+  float2* tsrc = tile + cpb * BS + cps;
+  if (cvalid) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) cp_async8(tsrc + i * S, gsrc + (size_t)i * rstride);
+  }
+  // ---- compute role: thread (s, b); its interface record is fetched while the tile lands
+  const int s = threadIdx.x / P, b = threadIdx.x - s * P;
+  const int kx = kx0 + s;
+  const int sys = kz * g.ncols + kx;
+  const bool active = kx < kx_hi && kx < g.ncols && !(kx == 0 && kz == 0) && !is_low(kx, kz, g.nz, low);
+  float vL = 0.f, inv = 0.f, X01 = 0.f, X10 = 0.f, tw = 0.f;
+  if (P > 1 && active && b < P - 1) {
+    const float* t = rtab + ((size_t)sys * (P - 1) + b) * 5;
+    vL = __ldg(t); inv = __ldg(t + 1); X01 = __ldg(t + 2); X10 = __ldg(t + 3); tw = __ldg(t + 4);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  scan_sweeps<M>(P, S, tile + b * BS + s, as + b * MS, csm + b * MS, b, active,
+                 active ? float(-(lamx[kx] + lamz[kz])) : 0.f, vL, inv, X01, X10, tw);
   __syncthreads();
   // ---- coalesced copy-out
   if (cvalid) {
