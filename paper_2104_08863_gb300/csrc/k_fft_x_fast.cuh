@@ -292,10 +292,11 @@ inline cudaError_t set_smem(K kernel, int smem) {
   return ensure_smem_limit((const void*)kernel, (size_t)smem);
 }
 
-// FP32 spectra of FP32 fields: the two-pass register kernels (k_fft_x_reg.cuh).  With FP64
-// fields (the FP64 right-hand side, the refinement residual, the FP64 assembly of the refined
-// pressure) the Stockham kernels measured faster: their epilogues are latency-bound and want the
-// occupancy that the register kernels (up to 128 registers per thread) do not leave.
+// FP32 spectra of FP32 fields: the two-pass register kernels (k_fft_x_reg.cuh); the refinement
+// residual (Nx/2 >= 256) too, with its residual formed warp by warp into shared memory first.
+// For the plain FP64 right-hand side and the FP64 assembly of the refined pressure the Stockham
+// kernels measured faster: those passes are latency-bound on their FP64 streams and want the
+// finer-grained CTAs (two lines, 63-80 registers) that the register kernels do not give.
 template <typename TI, int M>
 cudaError_t launch_fwd_x_reg(const Geometry& g, const DevTables& tb, FwdMode mode, const FwdArgs& args,
                              cplx<float>* spec, cudaStream_t st) {
@@ -386,6 +387,16 @@ cudaError_t launch_fwd_x_stockham(const Geometry& g, const DevTables& tb, const 
       return cudaGetLastError();
     }
   }
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8 && M >= 256) {
+    // refinement residual: warp-per-line residual into shared memory, then the register transform
+    if (mode == FWD_RESID) {
+      using R = XReg<M>;
+      auto k = k_fwd_x_reg_resid<M>;
+      if ((e = set_smem(k, R::SMEM)) != cudaSuccess) return e;
+      k<<<(nlines + R::LPB - 1) / R::LPB, R::THREADS, R::SMEM, st>>>(g, args, tt, tb, spec, nlines);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (sizeof(T) == sizeof(TI)) {
     switch (mode) {
       case FWD_PLAIN: PP_FWDF(FWD_PLAIN) break;
@@ -449,6 +460,8 @@ cudaError_t launch_inv_x_m(const Geometry& g, const DevTables& tb, const Tables<
 template <typename T, typename TI>
 cudaError_t launch_fwd_x_fast_impl(const Geometry& g, const DevTables& tb, const Tables<T>& tt, FwdMode mode,
                                    const FwdArgs& args, cplx<T>* spec, cudaStream_t st) {
+  // the per-line residual addresses its neighbour lines by 32-bit offsets
+  if (mode == FWD_RESID && (long long)g.nx * g.nz >= (1LL << 31)) return cudaErrorNotSupported;
   switch (g.M) {
 #define PP_CASE(MV) \
   case MV: return launch_fwd_x_m<T, TI, MV>(g, tb, tt, mode, args, spec, st);

@@ -1,4 +1,5 @@
-// Two-pass register x-transforms for FP32 spectra of FP32 fields (steps (2) and (8) of Sec. 3.2).
+// Two-pass register x-transforms for FP32 spectra of FP32 fields (steps (2) and (8) of Sec. 3.2),
+// and the forward transform of the refinement residual.
 //
 // The half-length complex transform of a line (M = Nx/2 = N1 x N2, N1 >= N2, both <= 32) is done
 // by threads that each hold a whole short transform in registers: pass 1 thread (t, n1) of line
@@ -107,6 +108,103 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 3)
                 int nlines) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fwd_x_reg_tile<TI, M, MODE>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
+}
+
+// Refinement residual r = (f - <f>) - L_h p (FP64 rhs f, FP32-pair pressure; resid_pair_line2)
+// transformed into the FP32 half spectrum.  Phase 0: one warp per line forms the residual pairs
+// in natural order in shared memory (the line's set-up amortised over M/32 pairs per lane, loads
+// coalesced across the warp); the register transform then reads its inputs from there (one more
+// barrier, since pass 1 overwrites the natural order with the transposed rows of the same line).
+template <int M>
+__device__ __forceinline__ void fwd_x_reg_resid_tile(const Geometry& g, const FwdArgs& args, const Tables<float>& tt,
+                                                     const DevTables& tb, cplx<float>* __restrict__ spec,
+                                                     int nlines, int tile, unsigned char* smem_raw) {
+  using C = XReg<M>;
+  constexpr int N1 = C::N1, N2 = C::N2, LPB = C::LPB, B = C::B, LS = C::LS, THREADS = C::THREADS;
+  constexpr int NW = THREADS / 32;   // whole warps (a partial last warp skips phase 0)
+  static_assert(NW >= 1, "at least one warp");
+  cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);
+  const int line0 = tile * LPB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < NW) {
+    float mh, ml;
+    f64_split(tb.acc[0], mh, ml);
+    for (int t = warp; t < LPB; t += NW) {
+      const int line = line0 + t;
+      cplx<float>* nat = buf + t * LS;
+      if (line < nlines) {
+        const ResidLine R = resid_line(g, args, tt, tb, line, mh, ml);
+#pragma unroll 3
+        for (int n = lane; n < M; n += 32) {
+          const float2 r = resid_pair_line2(R, n);
+          nat[n] = mk<float>(r.x, r.y);
+        }
+      } else {
+        for (int n = lane; n < M; n += 32) nat[n] = mk<float>(0.f, 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  const bool live = threadIdx.x < THREADS;
+  const int t = threadIdx.x / N1, n1 = threadIdx.x - t * N1;
+  cplx<float> v[N2];
+  if (live) {
+    const cplx<float>* nat = buf + t * LS + n1;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = nat[N1 * n2];
+  }
+  __syncthreads();
+  if (live) {
+    reg_dft<float, N2, -1>(v);
+    cplx<float>* row = buf + t * LS + n1;
+    static_for<0, N2>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      constexpr int k2 = reg_freq(N2, s);
+      cplx<float> x = v[s];
+      if constexpr (k2 != 0) x = cmul(x, ldg_c(tt.tw_m + n1 * k2));
+      row[k2 * B] = x;
+    });
+  }
+  __syncthreads();
+  constexpr int P2 = LPB * N2;   // pass-2 threads
+  cplx<float> u[N1];
+  const int t2 = threadIdx.x / N2, k2 = threadIdx.x - t2 * N2;
+  if (threadIdx.x < P2) {
+    const cplx<float>* row = buf + t2 * LS + k2 * B;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) u[q] = row[q];
+    reg_dft<float, N1, -1>(u);
+  }
+  __syncthreads();
+  if (threadIdx.x < P2) {
+    cplx<float>* nat = buf + t2 * LS + k2;
+    static_for<0, N1>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      nat[N2 * reg_freq(N1, s)] = u[s];
+    });
+  }
+  __syncthreads();
+  constexpr int M1 = M + 1;
+  if (live) {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < LPB * M1; idx += THREADS) {
+      const int tl = idx / M1, kx = idx - tl * M1;
+      const int line = line0 + tl;
+      if (line >= nlines) continue;
+      const cplx<float>* nat = buf + tl * LS;
+      const cplx<float> Zk = nat[kx == M ? 0 : kx];
+      const cplx<float> Zc = conj(nat[kx == 0 ? 0 : M - kx]);
+      st_c(spec + (size_t)line * g.pitch + kx, fwd_post(Zk, Zc, ldg_c(tt.tw_post + kx)));
+    }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(XReg<M>::THREADS, 3)
+    k_fwd_x_reg_resid(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
+                      int nlines) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fwd_x_reg_resid_tile<M>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
 }
 
 // Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE

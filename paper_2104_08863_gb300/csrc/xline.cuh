@@ -217,39 +217,40 @@ __device__ __forceinline__ void final_store(double* o, float2 h, float2 l, float
 }
 
 // ---- per-line form of the refinement residual (specialised kernels) --------------------------
-// Everything that depends only on the line (neighbour line pointers, double-float stencil
+// Everything that depends only on the line (neighbour line offsets, double-float stencil
 // coefficients, the split mean of f) is set up once per line.  The stencil sum is accumulated
 // in the compensated "Dot2" form (Ogita, Rump and Oishi, 2005): each product coef * d is split
 // exactly into p + pi by an FMA, the p are summed with TwoSum and all error terms go into one
 // correction, giving the result as if computed with twice the FP32 precision.
 struct ResidLine {
-  const float *P, *Pzm, *Pzp, *Pym, *Pyp;   // pressure hi: this line, z-1, z+1, y-1, y+1
-  const float *Q, *Qzm, *Qzp, *Qym, *Qyp;   // pressure lo (Q null when absent)
-  const double* f;
+  const float* P;      // pressure hi of this line
+  const float* Q;      // pressure lo of this line (null when absent)
+  const double* f;     // rhs of this line
+  int ozm, ozp;        // element offsets of the z-1 and z+1 lines (periodic)
+  int oym, oyp;        // offsets of the y-1 and y+1 lines (0 at a wall: no such face)
+  bool hym, hyp;       // the y-1 / y+1 face exists
   df cx, cz, ca, cc;
   float mh, ml;
   int nx;
 };
 
+// The offsets are 32-bit: the launchers send planes of 2^31 points or more to the generic kernels.
 template <typename TT>
 __device__ __forceinline__ ResidLine resid_line(const Geometry& g, const FwdArgs& args, const TT& tt,
                                                 const DevTables& tb, int line, float mh, float ml) {
   const int j = line / g.nz, k = line - j * g.nz;
-  const size_t nx = g.nx, plane = (size_t)g.nz * nx;
-  const size_t row = (size_t)line * nx;
-  const size_t rkm = ((size_t)j * g.nz + (k == 0 ? g.nz - 1 : k - 1)) * nx;
-  const size_t rkp = ((size_t)j * g.nz + (k + 1 == g.nz ? 0 : k + 1)) * nx;
-  const float* P = reinterpret_cast<const float*>(args.p);
-  const float* Q = reinterpret_cast<const float*>(args.plo);
+  const int plane = g.nz * g.nx;
+  const size_t row = (size_t)line * g.nx;
   ResidLine R;
-  R.P = P + row; R.Pzm = P + rkm; R.Pzp = P + rkp;
-  R.Pym = j >= 1 ? P + row - plane : nullptr;
-  R.Pyp = j + 1 <= g.ny - 1 ? P + row + plane : nullptr;
-  R.Q = Q ? Q + row : nullptr;
-  R.Qzm = Q ? Q + rkm : nullptr; R.Qzp = Q ? Q + rkp : nullptr;
-  R.Qym = (Q && R.Pym) ? Q + row - plane : nullptr;
-  R.Qyp = (Q && R.Pyp) ? Q + row + plane : nullptr;
+  R.P = reinterpret_cast<const float*>(args.p) + row;
+  R.Q = args.plo ? reinterpret_cast<const float*>(args.plo) + row : nullptr;
   R.f = reinterpret_cast<const double*>(args.in) + row;
+  R.ozm = (k == 0 ? g.nz - 1 : -1) * g.nx;
+  R.ozp = (k + 1 == g.nz ? 1 - g.nz : 1) * g.nx;
+  R.hym = j >= 1;
+  R.hyp = j + 1 <= g.ny - 1;
+  R.oym = R.hym ? -plane : 0;
+  R.oyp = R.hyp ? plane : 0;
   R.cx = df{args.idx2h, args.idx2l};
   R.cz = df{args.idz2h, args.idz2l};
   R.ca = df{tt.a[j], tt.a_lo[j]};
@@ -260,88 +261,13 @@ __device__ __forceinline__ ResidLine resid_line(const Geometry& g, const FwdArgs
   return R;
 }
 
-// (S, C) -= coef * (d.hi + d.lo), compensated.
-__device__ __forceinline__ void dot2_sub(float& S, float& C, df coef, df d) {
-  const float p = coef.hi * d.hi;
-  float q = fmaf(coef.hi, d.hi, -p);
-  q = fmaf(coef.lo, d.hi, q);
-  q = fmaf(coef.hi, d.lo, q);
-  const df s = two_sum_df(S, -p);
-  S = s.hi;
-  C += s.lo - q;
-}
-
 __device__ __forceinline__ float2 ld_f2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// a + b of two double-float differences: hi parts by TwoSum, low parts added (unnormalised;
-// the error is ~2^-48 of the larger difference, not of the pressure values).
-__device__ __forceinline__ df diff_sum(df a, df b) {
-  const df s = two_sum_df(a.hi, b.hi);
-  return df{s.hi, s.lo + (a.lo + b.lo)};
-}
-
-// Per cell: the neighbour differences of p = hi + lo, each exact (TwoDiff of the hi values, plus
-// TwoDiff of the lo values added by diff_sum), grouped by coefficient (x: both neighbours, z:
-// both neighbours, y: one per face), so that each group costs one compensated product; the
-// difference between the two cells of the pair is shared.
-__device__ __forceinline__ float2 resid_pair_line(const ResidLine& R, int n) {
-  const int i0 = 2 * n;
-  const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
-  const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
-  const float2 pc = ld_f2(R.P + i0);
-  const float pm = R.P[im], pp = R.P[ip];
-  const float2 zm = ld_f2(R.Pzm + i0), zp = ld_f2(R.Pzp + i0);
-  const float2 ym = R.Pym ? ld_f2(R.Pym + i0) : make_float2(0.f, 0.f);
-  const float2 yp = R.Pyp ? ld_f2(R.Pyp + i0) : make_float2(0.f, 0.f);
-  const double2 fv = *reinterpret_cast<const double2*>(R.f + i0);
-  float2 qc = make_float2(0.f, 0.f), qzm = qc, qzp = qc, qym = qc, qyp = qc;
-  float qm = 0.f, qp = 0.f;
-  if (R.Q) {
-    qc = ld_f2(R.Q + i0);
-    qm = R.Q[im];
-    qp = R.Q[ip];
-    qzm = ld_f2(R.Qzm + i0);
-    qzp = ld_f2(R.Qzp + i0);
-    if (R.Qym) qym = ld_f2(R.Qym + i0);
-    if (R.Qyp) qyp = ld_f2(R.Qyp + i0);
-  }
-  // p at cell 1 minus p at cell 0 (x-neighbours of each other)
-  df d01 = two_diff_df(pc.y, pc.x);
-  if (R.Q) d01 = diff_sum(d01, two_diff_df(qc.y, qc.x));
-  float out[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const float ctr = c ? pc.y : pc.x;
-    float fh, fl;
-    f64_split(c ? fv.y : fv.x, fh, fl);
-    const df s0 = two_sum_df(fh, -R.mh);
-    float S = s0.hi, C = s0.lo + (fl - R.ml);
-    // x: (p_{i+1} - p_i) + (p_{i-1} - p_i), one of them the shared d01
-    df dout = c ? two_diff_df(pp, ctr) : two_diff_df(pm, ctr);
-    df dz0 = two_diff_df(c ? zp.y : zp.x, ctr), dz1 = two_diff_df(c ? zm.y : zm.x, ctr);
-    df dy0 = two_diff_df(c ? ym.y : ym.x, ctr), dy1 = two_diff_df(c ? yp.y : yp.x, ctr);
-    if (R.Q) {
-      const float qctr = c ? qc.y : qc.x;
-      dout = diff_sum(dout, c ? two_diff_df(qp, qctr) : two_diff_df(qm, qctr));
-      dz0 = diff_sum(dz0, two_diff_df(c ? qzp.y : qzp.x, qctr));
-      dz1 = diff_sum(dz1, two_diff_df(c ? qzm.y : qzm.x, qctr));
-      if (R.Qym) dy0 = diff_sum(dy0, two_diff_df(c ? qym.y : qym.x, qctr));
-      if (R.Qyp) dy1 = diff_sum(dy1, two_diff_df(c ? qyp.y : qyp.x, qctr));
-    }
-    dot2_sub(S, C, R.cx, diff_sum(dout, c ? df_neg(d01) : d01));
-    dot2_sub(S, C, R.cz, diff_sum(dz0, dz1));
-    if (R.Pym) dot2_sub(S, C, R.ca, dy0);
-    if (R.Pyp) dot2_sub(S, C, R.cc, dy1);
-    out[c] = S + C;
-  }
-  return make_float2(out[0], out[1]);
-}
-
-// ---- the same residual with the two cells of a pair in packed FP32x2 operations ------------
+// ---- the residual of a pair of cells in packed FP32x2 operations -----------------------------
 // Each FP32x2 instruction performs the same correctly rounded operation on both lanes (cell 0
-// in .x, cell 1 in .y), so the double-float algorithms below are those of resid_pair_line
-// applied lane by lane, at half the issued instructions.  The *_rn intrinsics are never fused
-// into FMAs by the compiler, which the error-free transformations rely on.
+// in .x, cell 1 in .y), so the double-float algorithms below (TwoSum, TwoDiff, the FMA split of
+// a product, Dot2) run lane by lane at half the issued instructions.  The *_rn intrinsics are
+// never fused into FMAs by the compiler, which the error-free transformations rely on.
 struct df2 { float2 hi, lo; };
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -377,16 +303,36 @@ __device__ __forceinline__ void dot2_sub2(float2& S, float2& C, float2 ch, float
   C = f2add(C, f2sub(s.lo, q));
 }
 
-__device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
+// The loads of one pair (the pressure's hi values around the two cells and the rhs), issued
+// apart from the arithmetic so that a caller can keep the next pair's loads in flight.
+struct ResidIn {
+  float2 pc, zm, zp, ym, yp;
+  float pm, pp;
+  double2 fv;
+};
+__device__ __forceinline__ ResidIn resid_load(const ResidLine& R, int n) {
   const int i0 = 2 * n;
   const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
   const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
-  const float2 pc = ld_f2(R.P + i0);
-  const float pm = R.P[im], pp = R.P[ip];
-  const float2 zm = ld_f2(R.Pzm + i0), zp = ld_f2(R.Pzp + i0);
-  const float2 ym = R.Pym ? ld_f2(R.Pym + i0) : make_float2(0.f, 0.f);
-  const float2 yp = R.Pyp ? ld_f2(R.Pyp + i0) : make_float2(0.f, 0.f);
-  const double2 fv = *reinterpret_cast<const double2*>(R.f + i0);
+  ResidIn in;
+  in.pc = ld_f2(R.P + i0);
+  in.pm = R.P[im];
+  in.pp = R.P[ip];
+  in.zm = ld_f2(R.P + (i0 + R.ozm));
+  in.zp = ld_f2(R.P + (i0 + R.ozp));
+  in.ym = R.hym ? ld_f2(R.P + (i0 + R.oym)) : make_float2(0.f, 0.f);
+  in.yp = R.hyp ? ld_f2(R.P + (i0 + R.oyp)) : make_float2(0.f, 0.f);
+  in.fv = *reinterpret_cast<const double2*>(R.f + i0);
+  return in;
+}
+
+__device__ __forceinline__ float2 resid_pair_from(const ResidLine& R, int n, const ResidIn& in) {
+  const int i0 = 2 * n;
+  const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
+  const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
+  const float2 pc = in.pc, zm = in.zm, zp = in.zp, ym = in.ym, yp = in.yp;
+  const float pm = in.pm, pp = in.pp;
+  const double2 fv = in.fv;
   // x-neighbours: cell 0 pairs (p_{i-1}, p_{i+1} = cell 1), cell 1 pairs (p_{i+2}, p_i = cell 0);
   // the difference between the two cells is shared with opposite signs
   df2 dout = two_diff2(make_float2(pm, pp), pc);
@@ -396,16 +342,16 @@ __device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
   if (R.Q) {
     const float2 qc = ld_f2(R.Q + i0);
     const float qm = R.Q[im], qp = R.Q[ip];
-    const float2 qzm = ld_f2(R.Qzm + i0), qzp = ld_f2(R.Qzp + i0);
-    const float2 qym = R.Qym ? ld_f2(R.Qym + i0) : make_float2(0.f, 0.f);
-    const float2 qyp = R.Qyp ? ld_f2(R.Qyp + i0) : make_float2(0.f, 0.f);
+    const float2 qzm = ld_f2(R.Q + (i0 + R.ozm)), qzp = ld_f2(R.Q + (i0 + R.ozp));
+    const float2 qym = R.hym ? ld_f2(R.Q + (i0 + R.oym)) : make_float2(0.f, 0.f);
+    const float2 qyp = R.hyp ? ld_f2(R.Q + (i0 + R.oyp)) : make_float2(0.f, 0.f);
     dout = diff_sum2(dout, two_diff2(make_float2(qm, qp), qc));
     const df2 q01 = two_diff2(make_float2(qc.y, qc.x), qc);
     const df2 e01 = diff_sum2(d01, q01);
     dz0 = diff_sum2(dz0, two_diff2(qzp, qc));
     dz1 = diff_sum2(dz1, two_diff2(qzm, qc));
-    if (R.Qym) dy0 = diff_sum2(dy0, two_diff2(qym, qc));
-    if (R.Qyp) dy1 = diff_sum2(dy1, two_diff2(qyp, qc));
+    if (R.hym) dy0 = diff_sum2(dy0, two_diff2(qym, qc));
+    if (R.hyp) dy1 = diff_sum2(dy1, two_diff2(qyp, qc));
     dout = diff_sum2(dout, e01);
   } else {
     dout = diff_sum2(dout, d01);
@@ -417,9 +363,13 @@ __device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
   float2 S = s0.hi, C = f2add(s0.lo, f2sub(fl, make_float2(R.ml, R.ml)));
   dot2_sub2(S, C, make_float2(R.cx.hi, R.cx.hi), make_float2(R.cx.lo, R.cx.lo), dout);
   dot2_sub2(S, C, make_float2(R.cz.hi, R.cz.hi), make_float2(R.cz.lo, R.cz.lo), diff_sum2(dz0, dz1));
-  if (R.Pym) dot2_sub2(S, C, make_float2(R.ca.hi, R.ca.hi), make_float2(R.ca.lo, R.ca.lo), dy0);
-  if (R.Pyp) dot2_sub2(S, C, make_float2(R.cc.hi, R.cc.hi), make_float2(R.cc.lo, R.cc.lo), dy1);
+  if (R.hym) dot2_sub2(S, C, make_float2(R.ca.hi, R.ca.hi), make_float2(R.ca.lo, R.ca.lo), dy0);
+  if (R.hyp) dot2_sub2(S, C, make_float2(R.cc.hi, R.cc.hi), make_float2(R.cc.lo, R.cc.lo), dy1);
   return f2add(S, C);
+}
+
+__device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
+  return resid_pair_from(R, n, resid_load(R, n));
 }
 
 }  // namespace pp
