@@ -689,6 +689,67 @@ poisson_status predictor_impl(Exec& ex, void* u, void* v, void* w, void* ub, voi
   return PS_OK;
 }
 
+// The timestep of projection_timestep_host with its input copies overlapped: the rows of u, w and
+// the v faces go over in HOST_CHUNKS row chunks on the plan's copy stream, and momentum stage 1
+// of a chunk (Eqs. 5-6) starts on the caller's stream once the chunk and the row above it have
+// arrived (a stage-1 row reads its neighbours j-1 and j+1); the rest of the step follows as in
+// projection_timestep.
+poisson_status timestep_overlapped_input(poisson_plan_s* pl, const void* u_h, const void* v_h, const void* w_h,
+                                         void* u, void* v, void* w, void* ub, void* vb, void* wb, void* p_out,
+                                         double dt, double nu, double fx, cudaStream_t st) {
+  const Geometry& g = pl->g;
+  constexpr int C = pp::HOST_CHUNKS;
+  if (!pl->copy_st) {
+    if (cudaStreamCreateWithFlags(&pl->copy_st, cudaStreamNonBlocking) != cudaSuccess) return PS_ECUDA;
+    for (cudaEvent_t& e : pl->copy_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PS_ECUDA;
+  }
+  cudaStream_t cp = pl->copy_st;
+  // the copies start after the caller's earlier work on these buffers
+  if (cudaEventRecord(pl->copy_ev[C], st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamWaitEvent(cp, pl->copy_ev[C], 0) != cudaSuccess) return PS_ECUDA;
+  const size_t es = pl->precision == PP_FP32 ? 4 : 8;
+  const size_t plane = (size_t)g.nz * g.nx * es;
+  int rows[C + 1];
+  for (int c = 0; c <= C; ++c) rows[c] = (int)((long long)g.ny * c / C);
+  for (int c = 0; c < C; ++c) {
+    const size_t o = (size_t)rows[c] * plane, n = (size_t)(rows[c + 1] - rows[c]) * plane;
+    const size_t nvf = (c == C - 1 ? (size_t)(g.ny + 1 - rows[c]) : (size_t)(rows[c + 1] - rows[c])) * plane;
+    if (cudaMemcpyAsync((char*)u + o, (const char*)u_h + o, n, cudaMemcpyHostToDevice, cp) != cudaSuccess)
+      return PS_ECUDA;
+    if (cudaMemcpyAsync((char*)w + o, (const char*)w_h + o, n, cudaMemcpyHostToDevice, cp) != cudaSuccess)
+      return PS_ECUDA;
+    if (cudaMemcpyAsync((char*)v + o, (const char*)v_h + o, nvf, cudaMemcpyHostToDevice, cp) != cudaSuccess)
+      return PS_ECUDA;
+    if (cudaEventRecord(pl->copy_ev[c], cp) != cudaSuccess) return PS_ECUDA;
+  }
+  pl->launches = 0;
+  pl->nev = 0;
+  Exec ex{pl, pl->ws, pl->dt, st, false};
+  for (int c = 0; c < C; ++c) {
+    if (cudaStreamWaitEvent(st, pl->copy_ev[c + 1 < C ? c + 1 : C - 1], 0) != cudaSuccess) return PS_ECUDA;
+    if (pl->precision == PP_FP64) {
+      MomArgs<double> s1{(const double*)u, (const double*)v, (const double*)w, nullptr, nullptr, nullptr,
+                         (double*)ub, (double*)vb, (double*)wb, 0.0, 1.0, dt, nu, fx};
+      PP_TRY_N("momentum_1", launch_momentum<double>(g, ex.dt, s1, st, rows[c], rows[c + 1]));
+    } else {
+      MomArgs<float> s1{(const float*)u, (const float*)v, (const float*)w, nullptr, nullptr, nullptr,
+                        (float*)ub, (float*)vb, (float*)wb, 0.0, 1.0, dt, nu, fx};
+      PP_TRY_N("momentum_1", launch_momentum<float>(g, ex.dt, s1, st, rows[c], rows[c + 1]));
+    }
+  }
+  if (pl->precision == PP_FP64) {
+    MomArgs<double> s2{(const double*)ub, (const double*)vb, (const double*)wb, (const double*)u, (const double*)v,
+                       (const double*)w, (double*)u, (double*)v, (double*)w, 0.5, 0.5, 0.5 * dt, nu, fx};
+    PP_TRY_N("momentum_2", launch_momentum<double>(g, ex.dt, s2, st));
+  } else {
+    MomArgs<float> s2{(const float*)ub, (const float*)vb, (const float*)wb, (const float*)u, (const float*)v,
+                      (const float*)w, (float*)u, (float*)v, (float*)w, 0.5, 0.5, 0.5 * dt, nu, fx};
+    PP_TRY_N("momentum_2", launch_momentum<float>(g, ex.dt, s2, st));
+  }
+  return projection_impl(ex, u, v, w, p_out, dt);
+}
+
 }  // namespace
 
 namespace pp {
@@ -864,10 +925,17 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = pl->precision == PP_FP32 ? 4 : 8;
   const size_t nc = cell_count(pl) * es, nv = vface_count(pl) * es;
-  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-  PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
+  const bool overlap = pl->precision != PP_FP32_REFINED && !(pl->flags & (POISSON_CHECK_FINITE | POISSON_TIMING)) &&
+                       pl->g.ny >= 2 * pp::HOST_CHUNKS;
+  if (overlap) {
+    PP_RET(timestep_overlapped_input(pl, u_h, v_h, w_h, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx,
+                                     st));
+  } else {
+    if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+    if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+    if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+    PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
+  }
   if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
@@ -952,6 +1020,9 @@ poisson_status poisson_plan_destroy(poisson_plan_t pl) {
   if (pl) {
     for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
     if (pl->chain_st) cudaStreamDestroy(pl->chain_st);
+    if (pl->copy_st) cudaStreamDestroy(pl->copy_st);
+    for (cudaEvent_t e : pl->copy_ev)
+      if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : pl->chain_ev)
       if (e) cudaEventDestroy(e);
     pp::destroy_batch(pl);

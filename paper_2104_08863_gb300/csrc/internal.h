@@ -209,8 +209,11 @@ template <typename T> struct MomArgs {
   T *ou, *ov, *ow;
   double alpha, beta, bdt, nu, fx;
 };
+// Rows [jlo, jhi) of the cell fields and the v faces jlo .. jhi-1 (plus the wall faces 0 and ny
+// when the range touches them); jhi < 0: up to ny.  A range reads the rows jlo-1 .. jhi.
 template <typename T>
-cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st);
+cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st,
+                            int jlo = 0, int jhi = -1);
 
 // The FP64-accurate timestep on FP32 units (csrc/k_refined_ts.cu): the state as FP32 pairs
 // (hi, lo) in the FP64 buffers, double-float momentum stages, divergence and gradient.
@@ -229,6 +232,9 @@ cudaError_t launch_divergence_df(const Geometry& g, const DevTables& tb, const f
 // p in FP64.
 cudaError_t launch_gradient_pairs(const Geometry& g, const DevTables& tb, const float* hi, const float* lo, double* u,
                                   double* v, double* w, double* p_out, double dt, cudaStream_t st);
+
+// Row chunks of the host-buffer timestep's input copies (projection_timestep_host).
+constexpr int HOST_CHUNKS = 8;
 
 }  // namespace pp
 
@@ -254,6 +260,9 @@ struct poisson_plan_s {
   int chain_streams = 1;
   cudaStream_t chain_st = nullptr;
   cudaEvent_t chain_ev[2] = {nullptr, nullptr};
+  // host-buffer timestep: the stream of its input copies and one event per row chunk (+ a start)
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev[pp::HOST_CHUNKS + 1] = {};
   // POISSON_TIMING: one event pair around every launch of the last call
   std::vector<cudaEvent_t> ev;
   std::vector<const char*> ev_names;

@@ -39,12 +39,13 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum(Geometry g, MomArgs<T> a
                                                          const double* __restrict__ inv_dy,
                                                          const double* __restrict__ inv_h,
                                                          const double* __restrict__ lo,
-                                                         const double* __restrict__ up, int jc) {
+                                                         const double* __restrict__ up, int jlo, int jhi,
+                                                         int jc) {
   extern __shared__ unsigned char smem_raw[];
   RowCoef<T>* rc = reinterpret_cast<RowCoef<T>*>(smem_raw);
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int j0 = blockIdx.z * jc;
-  const int j1 = min(ny, j0 + jc);
+  const int j0 = jlo + blockIdx.z * jc;
+  const int j1 = min(jhi, j0 + jc);
   const double bdtnu = a.bdt * a.nu;
   const double cdx = bdtnu / (g.dx * g.dx), cdz = bdtnu / (g.dz * g.dz);
   for (int r = threadIdx.y * MTX + threadIdx.x; r < j1 - j0; r += MTX * MTZ) {
@@ -189,24 +190,30 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum(Geometry g, MomArgs<T> a
 }  // namespace
 
 template <typename T>
-cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st) {
+cudaError_t launch_momentum(const Geometry& g, const DevTables& tb, const MomArgs<T>& a, cudaStream_t st, int jlo,
+                            int jhi) {
+  if (jhi < 0) jhi = g.ny;
+  if (jlo < 0 || jhi > g.ny || jhi <= jlo) return cudaErrorInvalidValue;
+  const int rows = jhi - jlo;
   const int tx = (g.nx + MTX - 1) / MTX, tz = (g.nz + MTZ - 1) / MTZ;
   // enough CTAs for about three waves of two CTAs per SM; chunks of at least 16 rows
   const long long tiles = (long long)tx * tz;
   int chunks = (int)((3LL * 2 * 152 + tiles - 1) / tiles);
-  if (chunks > g.ny / 16) chunks = g.ny / 16;
+  if (chunks > rows / 16) chunks = rows / 16;
   if (chunks < 1) chunks = 1;
-  const int jc = (g.ny + chunks - 1) / chunks;
-  chunks = (g.ny + jc - 1) / jc;
+  const int jc = (rows + chunks - 1) / chunks;
+  chunks = (rows + jc - 1) / jc;
   const size_t smem = sizeof(RowCoef<T>) * (size_t)jc;
   const cudaError_t e = ensure_smem_limit((const void*)k_momentum<T>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(tx, tz, chunks), block(MTX, MTZ);
-  k_momentum<T><<<grid, block, smem, st>>>(g, a, tb.d.inv_dy, tb.d.inv_h, tb.d.a, tb.d.c, jc);
+  k_momentum<T><<<grid, block, smem, st>>>(g, a, tb.d.inv_dy, tb.d.inv_h, tb.d.a, tb.d.c, jlo, jhi, jc);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_momentum<double>(const Geometry&, const DevTables&, const MomArgs<double>&, cudaStream_t);
-template cudaError_t launch_momentum<float>(const Geometry&, const DevTables&, const MomArgs<float>&, cudaStream_t);
+template cudaError_t launch_momentum<double>(const Geometry&, const DevTables&, const MomArgs<double>&, cudaStream_t,
+                                             int, int);
+template cudaError_t launch_momentum<float>(const Geometry&, const DevTables&, const MomArgs<float>&, cudaStream_t,
+                                            int, int);
 
 }  // namespace pp

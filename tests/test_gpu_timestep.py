@@ -249,3 +249,59 @@ def test_refined_timestep_matches_oracle_over_three_steps(P, shape):
     assert relerr(pt.cpu().numpy(), p) <= 1e-10
     d = oracle.divergence(g, ut.cpu().numpy(), vt.cpu().numpy(), wt.cpu().numpy())
     assert np.max(np.abs(d)) <= 1e-10 * scale / min(g.dx, g.dz, g.dy.min())
+
+
+HOST_SHAPES = [  # (nx, ny, nz, stretch): rows not a multiple of the 8 copy chunks; ny < 16 (copies not chunked)
+    (48, 37, 24, 1.8),
+    (32, 64, 16, 2.0),
+    (24, 12, 8, 1.5),
+]
+
+
+@pytest.mark.parametrize("shape", HOST_SHAPES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "refined"])
+def test_host_timestep_equals_device_timestep(P, shape, prec):
+    """projection_timestep_host (pinned host buffers; the input rows copied in chunks beside the
+    first momentum stage) gives the device path's result bit for bit over two steps, and the
+    oracle's at the precision's tolerance."""
+    nx, ny, nz, s = shape
+    case = W.ChannelCase("t", nx, ny, nz, s)
+    faces = W.tanh_faces(ny, s)
+    g = oracle.Grid(nx, nz, faces)
+    u, v, w = W.poiseuille_plus_noise(1, case)
+    dt = 1e-3
+    precision = {"fp64": P.PP_FP64, "fp32": P.PP_FP32, "refined": P.PP_FP32_REFINED}[prec]
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    plan = P.Plan(nx, ny, nz, faces, precision=precision, refine_steps=2 if prec == "refined" else 1, device=DEV)
+    ut, vt, wt = (to_dev(a, dtype) for a in (u, v, w))
+    pt = torch.empty(ny, nz, nx, dtype=dtype, device=DEV)
+    scratch = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    hosts = [torch.from_numpy(np.ascontiguousarray(a)).to(dtype).pin_memory() for a in (u, v, w)]
+    ph = torch.empty(ny, nz, nx, dtype=dtype).pin_memory()
+    staging = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt), torch.empty_like(pt))
+    scratch_h = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    ref = (u, v, w)
+    for _ in range(2):
+        plan.timestep(ut, vt, wt, dt, NU, FX, p_out=pt, scratch=scratch)
+        plan.timestep_host(*hosts, dt, NU, FX, staging, scratch_h, p_h=ph)
+        ref = timestep(g, *ref[:3], dt, NU, FX)
+    torch.cuda.synchronize()
+    for q, (dev_t, host_t) in enumerate(zip((ut, vt, wt, pt), (*hosts, ph))):
+        if prec == "refined":
+            # the refined solve's gauge sums its pressure with FP64 atomics, whose order (and so
+            # the last bits of the gauge constant carried in the pressure's low FP32 part) varies
+            # from run to run; that reaches u at the rounding level and the next step's pressure
+            # amplified as described below
+            d = float((dev_t.cpu() - host_t).abs().max() / host_t.abs().max())
+            assert d <= (1e-13 if q < 3 else 1e-10), (q, d)
+        else:
+            assert torch.equal(dev_t.cpu(), host_t)
+    # velocities at the tolerances of the tests above; the pressure of a timestep solves for the
+    # divergence of u*, which is only the predictor's increment, so the rounding of u* reaches p
+    # amplified by |u| / (dt |R|) ~ 10^2-10^3 (see the refined timestep test): 1e-10 in FP64 and
+    # the refined form, 1e-3 in FP32 (its 6e-8 rounding of u* after two steps)
+    tol = 2e-5 if prec == "fp32" else 1e-12
+    scale = max(np.max(np.abs(a)) for a in ref[:3])
+    for got, want in zip(hosts, ref[:3]):
+        assert float(np.max(np.abs(got.double().numpy() - want))) / scale <= tol
+    assert relerr(ph.double().numpy(), ref[3]) <= (1e-3 if prec == "fp32" else 1e-10)
