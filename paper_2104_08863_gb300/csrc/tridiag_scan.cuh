@@ -82,7 +82,11 @@ __device__ __forceinline__ void scan_sweeps(int P, int S, float2* blk, const flo
                                             bool active, float sigma, float vL, float inv, float X01, float X10,
                                             float tw) {
   const int lseg = b;
-  float rbv[M], gvv[M];
+  // The backward sweep x_i = rb_i (gg_i + alpha gv_i + c_i x_{i+1}) takes its three products with
+  // the pivot reciprocal rb_i from the forward sweep: rb_i gg_i in the tile (in place of gg_i),
+  // rb_i c_i and rb_i gv_i in registers, so that it loads no coefficient from shared memory (whose
+  // bandwidth bounds both sweeps).
+  float rcv[M], rgv[M];
   float2 xF = make_float2(0.f, 0.f), xL = make_float2(0.f, 0.f);
   if (active) {
     float e = ab[0] + sigma, gv = ab[0], rb = rcp_nr(cb[0] + e);
@@ -100,13 +104,14 @@ __device__ __forceinline__ void scan_sweeps(int P, int S, float2* blk, const flo
         rb = rcp_nr(cj + e);
       }
       gg = make_float2(fmaf(mult, gg.x, -F.x), fmaf(mult, gg.y, -F.y));
-      blk[i * S] = gg;
-      rbv[i] = rb;
-      gvv[i] = gv;
+      blk[i * S] = make_float2(gg.x * rb, gg.y * rb);
+      const float crb = cj * rb;
+      rcv[i] = crb;
+      rgv[i] = gv * rb;
       const float kap = run * rb;
       xF.x = fmaf(kap, gg.x, xF.x);
       xF.y = fmaf(kap, gg.y, xF.y);
-      run *= cj * rb;
+      run *= crb;
     }
     xL = make_float2(gg.x * rb, gg.y * rb);
   }
@@ -137,11 +142,9 @@ __device__ __forceinline__ void scan_sweeps(int P, int S, float2* blk, const flo
     float2 xn = beta;
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
-      const float cj = cb[i];
-      const float2 G2 = blk[i * S];
-      const float tx = fmaf(cj, xn.x, fmaf(alpha.x, gvv[i], G2.x));
-      const float ty = fmaf(cj, xn.y, fmaf(alpha.y, gvv[i], G2.y));
-      xn = make_float2(tx * rbv[i], ty * rbv[i]);
+      const float2 G2 = blk[i * S];   // rb_i gg_i
+      xn = make_float2(fmaf(rcv[i], xn.x, fmaf(rgv[i], alpha.x, G2.x)),
+                       fmaf(rcv[i], xn.y, fmaf(rgv[i], alpha.y, G2.y)));
       blk[i * S] = xn;
     }
   }
