@@ -2,14 +2,15 @@
 // arithmetic on FP32 units.
 //
 // On GB300 an FP64 arithmetic instruction and an F2F conversion both issue at about two per
-// clock per SM, against 128 FP32 and 64 integer operations, so the FP32-refined solve keeps
-// every per-point operation off the FP64 pipe:
+// clock per SM, against 128 FP32 and 64 integer operations, so the FP32-refined solve keeps the
+// per-point work on the FP32 and integer pipes, with at most one FP64 addition per output value:
 //  * f64_to_f32_trunc / f64_split: a double's sign, exponent and top 24 significand bits give
 //    hi; the remaining 29 bits, converted by I2F and scaled by a power of two built in the
 //    exponent field, give lo, so hi + lo equals x to about 2^-47 relative.  Zeros, values below
 //    the FP32 normal range (flushed to zero) and values above it (to +-inf) are handled.
-//  * f32_sum_to_f64: a + b as a double within one FP64 ulp: the FP32 sum and its exact TwoSum
-//    error are placed into one 53-bit significand with integer operations.
+//  * f32_to_f64_exact / f32_add_to_f64: an FP32 value widened to FP64 by integer operations
+//    (exact), and a + b as one correctly rounded FP64 addition of two such widenings (exact for
+//    the two parts of a normalised pair).
 //  * two_sum / two_diff (Knuth), two_prod (by FMA), df_add, df_mul: the classical
 //    double-float algorithms (Dekker 1971, Knuth TAOCP vol. 2), accurate to about 2^-47.
 // Everything is __host__ __device__ so that the host test suite can check it bit for bit.
@@ -97,39 +98,24 @@ __host__ __device__ __forceinline__ void f64_split(double x, float& hi, float& l
   lo = (u >> 63) ? -mag : mag;
 }
 
-// a + b as a double, faithfully rounded (error below one FP64 ulp), by integer operations: the
-// FP32 sum s and its exact error e (TwoSum, |e| <= ulp(s)/2) are placed into one 53-bit
-// significand, s in the top 24 bits and e (aligned and truncated) in the low 29; a borrow from an
-// opposite-signed e renormalises by one bit.  FP32 subnormals are treated as zero.
-// s + e as a double for a normalised pair (|e| <= ulp(s)/2, e.g. the result of TwoSum or of a
-// double-float addition): the placement step of f32_sum_to_f64 alone.
-__host__ __device__ __forceinline__ double f32_norm_pair_to_f64(float s, float e) {
-  const uint32_t us = bits_of(s), ue = bits_of(e);
-  const uint32_t es = (us >> 23) & 0xffu, ee = (ue >> 23) & 0xffu;
-  if (es == 0u) return 0.0;
-  uint64_t R = (uint64_t)((us & 0x7fffffu) | 0x800000u) << 29;
-  int ex = (int)es + 896;   // FP64 biased exponent of s
-  if (ee != 0u) {
-    const uint32_t me = (ue & 0x7fffffu) | 0x800000u;
-    const int sh = (int)ee - (int)es + 29;   // <= 5
-    const uint32_t eu = sh >= 0 ? (me << sh) : (sh > -32 ? (me >> -sh) : 0u);
-    if ((us ^ ue) >> 31) {
-      R -= eu;
-      if (!(R >> 52)) {
-        R <<= 1;
-        --ex;
-      }
-    } else {
-      R += eu;
-    }
-  }
-  return double_of(((uint64_t)(us >> 31) << 63) | ((uint64_t)ex << 52) | (R & 0xfffffffffffffull));
+// x widened to FP64 exactly, by integer operations (an F2F conversion would run on the FP64
+// pipe): sign, exponent rebiased by +896 (255 -> 2047 for infinities and NaNs), the 23 fraction
+// bits at the top of the 52.  FP32 subnormals become zeros of the same sign.
+__host__ __device__ __forceinline__ double f32_to_f64_exact(float x) {
+  const uint32_t u = bits_of(x);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t sign = u & 0x80000000u;
+  if (e == 0u) return double_of((uint64_t)sign << 32);
+  const uint32_t ee = e == 0xffu ? 0x7ffu : e + 896u;
+  const uint32_t h = sign | (ee << 20) | ((u >> 3) & 0xfffffu);
+  return double_of(((uint64_t)h << 32) | (uint64_t)(u << 29));
 }
 
-__host__ __device__ __forceinline__ double f32_sum_to_f64(float a, float b) {
-  const float s = a + b;
-  const float bp = s - a;
-  return f32_norm_pair_to_f64(s, (a - (s - bp)) + (b - bp));
+// a + b as a double: one correctly rounded FP64 addition of the exact widenings, the only FP64
+// instruction of the conversion.  Exact when b lies within 29 bits below a, as the low part of a
+// normalised pair does.
+__host__ __device__ __forceinline__ double f32_add_to_f64(float a, float b) {
+  return f32_to_f64_exact(a) + f32_to_f64_exact(b);
 }
 
 // ---- double-float arithmetic (value = hi + lo) ----------------------------------------------

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_to_pairs(double* __restrict__ x, size_t
 __global__ void __launch_bounds__(256) k_from_pairs(double* __restrict__ x, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float2 v = reinterpret_cast<const float2*>(x)[i];
-    x[i] = f32_sum_to_f64(v.x, v.y);
+    x[i] = f32_add_to_f64(v.x, v.y);
   }
 }
 
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_divergence_df(Geometry g, const float2*
       df s = dmul(cx, dsub(ldp(u + oxp), ldp(u + idx)));
       s = dfma(cz, dsub(ldp(w + ozp), ldp(w + idx)), s);
       s = dfma(cy, dsub(ldp(v + idx + plane), ldp(v + idx)), s);
-      f[idx] = f32_norm_pair_to_f64(s.hi, s.lo);
+      f[idx] = f32_add_to_f64(s.hi, s.lo);
     }
   }
 }
@@ -283,17 +283,17 @@ __global__ void __launch_bounds__(256) k_gradient_pairs(Geometry g, const float*
         const df pzm = P((size_t)j * plane + (size_t)(k == 0 ? g.nz - 1 : k - 1) * g.nx + i);
         const df un = dsub(df{uu.x, uu.y}, dmul(cx, dsub(pc, pxm)));
         const df wn = dsub(df{ww.x, ww.y}, dmul(cz, dsub(pc, pzm)));
-        u[idx] = f32_norm_pair_to_f64(un.hi, un.lo);
-        w[idx] = f32_norm_pair_to_f64(wn.hi, wn.lo);
-        if (p_out) p_out[idx] = f32_sum_to_f64(pc.hi, pc.lo);
+        u[idx] = f32_add_to_f64(un.hi, un.lo);
+        w[idx] = f32_add_to_f64(wn.hi, wn.lo);
+        if (p_out) p_out[idx] = f32_add_to_f64(pc.hi, pc.lo);
         if (j >= 1) {
           vn = dsub(vn, dmul(cy, dsub(pc, P(idx - plane))));
-          v[idx] = f32_norm_pair_to_f64(vn.hi, vn.lo);
+          v[idx] = f32_add_to_f64(vn.hi, vn.lo);
         } else {
-          v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
+          v[idx] = f32_add_to_f64(vn.hi, vn.lo);
         }
       } else {
-        v[idx] = f32_sum_to_f64(vn.hi, vn.lo);
+        v[idx] = f32_add_to_f64(vn.hi, vn.lo);
       }
     }
   }

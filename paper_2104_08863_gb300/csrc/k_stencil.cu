@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_weighted_pair(Geometry g, const float* 
     const double w = dy[line / g.nz];
     const size_t base = (size_t)line * g.nx;
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
-      q[base + i] = w * f32_sum_to_f64(hi[base + i], lo ? lo[base + i] : 0.0f);
+      q[base + i] = w * f32_add_to_f64(hi[base + i], lo ? lo[base + i] : 0.0f);
   }
 }
 

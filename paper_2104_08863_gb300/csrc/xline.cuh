@@ -204,7 +204,7 @@ __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const P
       const float2 h = *reinterpret_cast<const float2*>(pair.hi + off);
       float2 l = make_float2(0.0f, 0.0f);
       if (pair.lo) l = *reinterpret_cast<const float2*>(pair.lo + off);
-      RealIO<TO>::store2(o, f32_sum_to_f64(h.x, l.x + x0), f32_sum_to_f64(h.y, l.y + x1));
+      RealIO<TO>::store2(o, f32_add_to_f64(h.x, l.x + x0), f32_add_to_f64(h.y, l.y + x1));
     }
   } else {
     RealIO<TO>::store2(o, TO(x0), TO(x1));
@@ -212,8 +212,12 @@ __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const P
 }
 
 // INV_FINAL epilogue on preloaded pairs: p = hi + (lo + v), v the last correction.
+// hi + (lo + v) in FP64: both FP32 terms widened exactly by integer operations and added by one
+// FP64 addition (correctly rounded), which costs fewer issue slots than assembling the sum by
+// integer operations and runs on the FP64 pipe, idle in this pass.
 __device__ __forceinline__ void final_store(double* o, float2 h, float2 l, float v0, float v1) {
-  RealIO<double>::store2(o, f32_sum_to_f64(h.x, l.x + v0), f32_sum_to_f64(h.y, l.y + v1));
+  RealIO<double>::store2(o, f32_to_f64_exact(h.x) + f32_to_f64_exact(l.x + v0),
+                         f32_to_f64_exact(h.y) + f32_to_f64_exact(l.y + v1));
 }
 
 // ---- per-line form of the refinement residual (specialised kernels) --------------------------

@@ -20,7 +20,9 @@ int main() {
       f64_split(x, hi, lo);
       std::printf("%08x %08x\n", bits_of(hi), bits_of(lo));
     } else if (!std::strcmp(op, "sum")) {    // x, y carry FP32 values widened to FP64
-      std::printf("%016llx\n", (unsigned long long)bits_of(f32_sum_to_f64((float)x, (float)y)));
+      std::printf("%016llx\n", (unsigned long long)bits_of(f32_add_to_f64((float)x, (float)y)));
+    } else if (!std::strcmp(op, "widen")) {  // x carries an FP32 value widened to FP64
+      std::printf("%016llx\n", (unsigned long long)bits_of(f32_to_f64_exact((float)x)));
     } else if (!std::strcmp(op, "dfadd") || !std::strcmp(op, "dfmul")) {
       float xh, xl, yh, yl;
       f64_split(x, xh, xl);

@@ -80,10 +80,10 @@ def test_split_is_accurate_to_47_bits(prog):
         assert abs(hi) <= abs(x)
 
 
-def test_sum_to_double_is_faithful(prog):
-    """f32_sum_to_f64: within one FP64 ulp of the exact sum, including cancellation, a power-of-two
-    s with an opposite-signed error term, zero error terms and operands of very different size
-    (FP32 subnormal error terms are flushed, so the bound adds 2^-126 there)."""
+def test_sum_to_double_is_correctly_rounded(prog):
+    """f32_add_to_f64: the exact sum rounded to nearest FP64 (half an ulp), including cancellation,
+    operands of very different size and the two parts of normalised pairs (exact there); FP32
+    subnormal operands are flushed, so the bound adds 2^-126 for them."""
     rng = np.random.default_rng(6)
     a = (rng.standard_normal(4000) * 10.0 ** rng.uniform(-20, 20, 4000)).astype(np.float32)
     rel = 10.0 ** rng.uniform(-14, 3, 4000)
@@ -100,7 +100,25 @@ def test_sum_to_double_is_faithful(prog):
             assert got == 0.0
             continue
         ulp = Fraction(np.spacing(abs(float(exact))))
-        assert abs(Fraction(got) - exact) <= ulp + Fraction(1, 2 ** 126), (x, y, got, float(exact))
+        assert abs(Fraction(got) - exact) <= ulp / 2 + Fraction(1, 2 ** 126), (x, y, got, float(exact))
+
+
+def test_widening_to_double_is_exact(prog):
+    """f32_to_f64_exact: the FP64 value of every normal FP32 input (and of zeros, infinities and a
+    NaN) bit for bit; FP32 subnormals become signed zeros."""
+    rng = np.random.default_rng(8)
+    bits = rng.integers(0, 2 ** 32, 20000, dtype=np.uint64).astype(np.uint32)
+    vals = list(bits.view(np.float32)) + [np.float32(v) for v in (0.0, -0.0, 1.0, -2.5, 3.4e38, -1.2e-38)]
+    vals += [np.float32(np.inf), np.float32(-np.inf), np.float32(1e-40), np.float32(-1e-45)]
+    outs = run(prog, [f"widen {d2h(float(v)):016x} 0000000000000000" for v in vals])
+    for v, o in zip(vals, outs):
+        got = h2d(o)
+        if np.isnan(v):
+            assert np.isnan(got)
+        elif v != 0 and abs(float(v)) < 2.0 ** -126:
+            assert got == 0.0 and np.signbit(got) == np.signbit(v)
+        else:
+            assert d2h(got) == d2h(float(v)), (v, o)
 
 
 @pytest.mark.parametrize("op", ["dfadd", "dfmul"])

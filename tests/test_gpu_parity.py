@@ -342,6 +342,23 @@ def test_fp32_refined_solve_ragged_staged_tiles(P):
     assert plan.device_status() == 0
 
 
+@pytest.mark.parametrize("nx,ny,nz,steps", [(768, 5, 9, 1), (768, 4, 6, 2), (1024, 3, 6, 2), (2048, 5, 3, 1)])
+def test_fp32_refined_solve_register_residual_lengths(P, nx, ny, nz, steps):
+    """The residual pass with the register transform at Nx/2 = 384 (240 threads: a partial last
+    warp skips the residual phase; tiles of 10 lines), 512 and 1024, every line count leaving a
+    ragged last tile; one correction at the one-correction bound, two at the FP64 bar."""
+    faces = W.tanh_faces(ny, 1.7)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(7, nx, ny, nz))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=1, fp64_low_modes=4,
+                  refine_steps=steps, device=DEV)
+    got = plan.solve(to_dev(f))
+    torch.cuda.synchronize()
+    assert relerr(got.cpu().numpy(), want) <= (2e-9 if steps == 1 else 1e-12)
+    assert plan.device_status() == 0
+
+
 def test_bounded_wait_runs_out_and_reports_timeout(P):
     """POISSON_SELFTEST_WAIT makes the bulk-copy-staged x-transform skip its first copy: its
     bounded mbarrier wait gives up (~2 s), the device status reads PS_ETIMEOUT, and the context
