@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 3)
 }
 
 // Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE
-// (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1], formed in double-float arithmetic on the
-// FP32 units (one FP64 atomic per warp).
+// (INV_STORE, INV_ACCUM); ACC also adds the dy-weighted sum of the result to acc[1], formed in
+// double-float arithmetic on the FP32 units (one FP64 atomic per warp).
 template <typename TO, int M, int MODE, bool ACC>
 __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<float>& tt,
                                                const cplx<float>* __restrict__ spec, TO* __restrict__ out,
@@ -266,7 +266,8 @@ __device__ __forceinline__ void inv_x_reg_tile(const Geometry& g, const Tables<f
     reg_dft<float, N1, 1>(u);
     const float s = float(scl);
     const size_t o0 = (size_t)line * g.nx + 2 * k2;
-    // compensated sums of the even and the odd outputs, two independent chains per lane
+    // compensated sums with the pair (x0, x1) in the two lanes of packed FP32x2 operations, the
+    // thread's successive outputs alternating between two independent chains
     float2 hs[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     float2 hc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     static_for<0, N1>([&](auto sc) {
