@@ -524,6 +524,13 @@ def mode_coeffs_gpu(p, kx, kz):
     return (re + 1j * im).cpu().numpy()
 
 
+# Algorithmic HBM bytes per grid point of the precision forms at 1536x768x1024: FP64 plain 48
+# (58.0 GB: read f, write and read F, write and read P, write p), FP32 plain 24 (29.0 GB), FP32
+# with one FP64-residual correction 80 (96.7 GB: both solves, the FP64 rhs read twice, the FP32
+# pressure written and read back, the FP64 pressure written).
+FORM_MODEL_BYTES_PER_POINT = {"fp64": 48, "fp32": 24, "fp32_refined_1": 80}
+
+
 def precision_forms(dev, steps: int = 5, warmup: int = 3):
     """FP64 plain vs FP32 vs FP32-refined Poisson solves on the 1536 x 768 x 1024 channel.
 
@@ -540,6 +547,7 @@ def precision_forms(dev, steps: int = 5, warmup: int = 3):
     case = W.CHANNEL_1536
     faces = W.tanh_faces(case.ny, case.stretch)
     golden = golden_modes_1536()
+    hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
     plans = {}
     mk = lambda prec, rs, flags=0: P.Plan(case.nx, case.ny, case.nz, faces, case.lx, case.lz, precision=prec,
                                           fp64_low_modes=4, refine_steps=max(rs, 1), flags=flags, device=dev)
@@ -580,6 +588,15 @@ def precision_forms(dev, steps: int = 5, warmup: int = 3):
         del tplan
         entry = {"ms": ms, "gpts_s": case.npoints / (ms * 1e-3) / 1e9,
                  "stage_ms": {k: round(v, 4) for k, v in sorted(stage.items(), key=lambda kv: -kv[1])}}
+        if name in FORM_MODEL_BYTES_PER_POINT:
+            model = FORM_MODEL_BYTES_PER_POINT[name] * case.npoints
+            achieved = model / (ms * 1e-3) / 1e9
+            entry["hbm_roofline"] = {"model_bytes": model, "achieved_gbs": achieved, "peak_gbs": hbm_peak,
+                                     "frac": achieved / hbm_peak,
+                                     "model": "six-transfer algorithmic bytes of the form (read f, write and "
+                                              "read the spectrum twice, write p; the refined form adds the "
+                                              "residual pass and the correction solve)",
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
         pmax = float(p.abs().max())
         worst = 0.0
         for kx, kz, want in golden:
