@@ -186,9 +186,11 @@ poisson_status projection_timestep(poisson_plan_t plan, void* u, void* v, void* 
  * u, v, w to the device buffers u_dev, v_dev, w_dev, runs projection_timestep with the device
  * scratch ub, vb, wb, copies u, v, w (and p when p_host != NULL, through p_dev) back and
  * synchronises `stream`.  For PP_FP64 and PP_FP32 plans with Ny >= 16 (and neither
- * POISSON_CHECK_FINITE nor POISSON_TIMING) the input copies go in 8 row chunks on a stream the
- * plan owns, and the first momentum stage of each row chunk starts on `stream` once its rows and
- * the row above have arrived; the results are those of projection_timestep bit for bit.  Host
+ * POISSON_CHECK_FINITE nor POISSON_TIMING) the copies go in 8 row chunks on a stream the plan
+ * owns: the first momentum stage of each row chunk starts on `stream` once its rows and the row
+ * above have arrived, and the inverse x-transform and the gradient correction run chunk by chunk
+ * with each chunk of p, u, v, w copied back while the next is computed; the results are those of
+ * projection_timestep bit for bit.  Host
  * buffers should be pinned (pageable memory is copied synchronously by CUDA and loses the
  * overlap).  The plan must not be used from two host threads at once. */
 poisson_status projection_timestep_host(poisson_plan_t plan, void* u_host, void* v_host, void* w_host,

@@ -689,14 +689,33 @@ poisson_status predictor_impl(Exec& ex, void* u, void* v, void* w, void* ub, voi
   return PS_OK;
 }
 
-// The timestep of projection_timestep_host with its input copies overlapped: the rows of u, w and
-// the v faces go over in HOST_CHUNKS row chunks on the plan's copy stream, and momentum stage 1
-// of a chunk (Eqs. 5-6) starts on the caller's stream once the chunk and the row above it have
-// arrived (a stage-1 row reads its neighbours j-1 and j+1); the rest of the step follows as in
-// projection_timestep.
-poisson_status timestep_overlapped_input(poisson_plan_s* pl, const void* u_h, const void* v_h, const void* w_h,
-                                         void* u, void* v, void* w, void* ub, void* vb, void* wb, void* p_out,
-                                         double dt, double nu, double fx, cudaStream_t st) {
+// The inverse x-transform (STORE) of the wall-normal rows [j0, j1): the lines of those rows are
+// one contiguous stretch of the spectrum and of the output, so the launch takes them as a grid of
+// j1 - j0 rows (the STORE form depends on nothing else of the row index).
+template <typename T>
+poisson_status inverse_x_rows(Exec& ex, T* out, int j0, int j1) {
+  const Geometry& g = ex.pl->g;
+  Geometry gs = g;
+  gs.ny = j1 - j0;
+  cplx<T>* spec = (cplx<T>*)(ex.ws + ex.pl->off_spec) + (size_t)j0 * g.nz * g.pitch;
+  const double scale = 1.0 / ((double)g.nx * (double)g.nz);
+  PP_TRY_N("inv_x", (launch_inv_x<T, T>(gs, ex.dt, ex.pl->fm, INV_STORE, spec, out + (size_t)j0 * g.nz * g.nx, scale,
+                                        false, ex.st, PairArgs{nullptr, nullptr})));
+  return PS_OK;
+}
+
+// projection_timestep_host of PP_FP64 and PP_FP32 plans with its copies overlapped.  The rows of
+// u, w and the v faces go over in HOST_CHUNKS row chunks on the plan's copy stream, and momentum
+// stage 1 of a chunk (Eqs. 5-6) starts on the caller's stream once the chunk and the row above it
+// have arrived (a stage-1 row reads its neighbours j-1 and j+1).  Stage 2 and the solve follow as
+// in projection_timestep; the inverse x-transform and the gradient correction (Eq. 4) then run
+// chunk by chunk, and each chunk of p (final after its inverse transform) and of u, v, w (final
+// after its gradient, which reads p rows j-1 and j) goes back to the host while the next chunk is
+// computed.  The results are those of projection_timestep bit for bit.
+template <typename T>
+poisson_status timestep_overlapped(poisson_plan_s* pl, const void* u_h, const void* v_h, const void* w_h, void* p_h,
+                                   T* u, T* v, T* w, T* ub, T* vb, T* wb, T* p_dev, double dt, double nu, double fx,
+                                   cudaStream_t st) {
   const Geometry& g = pl->g;
   constexpr int C = pp::HOST_CHUNKS;
   if (!pl->copy_st) {
@@ -705,49 +724,60 @@ poisson_status timestep_overlapped_input(poisson_plan_s* pl, const void* u_h, co
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PS_ECUDA;
   }
   cudaStream_t cp = pl->copy_st;
+  cudaEvent_t* ev_in = pl->copy_ev;             // input chunk c has arrived
+  cudaEvent_t ev_start = pl->copy_ev[C];
+  cudaEvent_t* ev_p = pl->copy_ev + C + 1;      // p rows of chunk c are final
+  cudaEvent_t* ev_g = pl->copy_ev + 2 * C + 1;  // u, v, w rows of chunk c are final
   // the copies start after the caller's earlier work on these buffers
-  if (cudaEventRecord(pl->copy_ev[C], st) != cudaSuccess) return PS_ECUDA;
-  if (cudaStreamWaitEvent(cp, pl->copy_ev[C], 0) != cudaSuccess) return PS_ECUDA;
-  const size_t es = pl->precision == PP_FP32 ? 4 : 8;
-  const size_t plane = (size_t)g.nz * g.nx * es;
+  if (cudaEventRecord(ev_start, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaStreamWaitEvent(cp, ev_start, 0) != cudaSuccess) return PS_ECUDA;
+  const size_t plane = (size_t)g.nz * g.nx;
   int rows[C + 1];
   for (int c = 0; c <= C; ++c) rows[c] = (int)((long long)g.ny * c / C);
+  // chunk c: cell rows [rows[c], rows[c+1]); v faces the same, plus the top wall face in the last
+  auto cells = [&](int c) { return (size_t)(rows[c + 1] - rows[c]) * plane; };
+  auto faces = [&](int c) { return (size_t)((c == C - 1 ? g.ny + 1 : rows[c + 1]) - rows[c]) * plane; };
   for (int c = 0; c < C; ++c) {
-    const size_t o = (size_t)rows[c] * plane, n = (size_t)(rows[c + 1] - rows[c]) * plane;
-    const size_t nvf = (c == C - 1 ? (size_t)(g.ny + 1 - rows[c]) : (size_t)(rows[c + 1] - rows[c])) * plane;
-    if (cudaMemcpyAsync((char*)u + o, (const char*)u_h + o, n, cudaMemcpyHostToDevice, cp) != cudaSuccess)
+    const size_t o = (size_t)rows[c] * plane;
+    if (cudaMemcpyAsync(u + o, (const T*)u_h + o, cells(c) * sizeof(T), cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+        cudaMemcpyAsync(w + o, (const T*)w_h + o, cells(c) * sizeof(T), cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+        cudaMemcpyAsync(v + o, (const T*)v_h + o, faces(c) * sizeof(T), cudaMemcpyHostToDevice, cp) != cudaSuccess)
       return PS_ECUDA;
-    if (cudaMemcpyAsync((char*)w + o, (const char*)w_h + o, n, cudaMemcpyHostToDevice, cp) != cudaSuccess)
-      return PS_ECUDA;
-    if (cudaMemcpyAsync((char*)v + o, (const char*)v_h + o, nvf, cudaMemcpyHostToDevice, cp) != cudaSuccess)
-      return PS_ECUDA;
-    if (cudaEventRecord(pl->copy_ev[c], cp) != cudaSuccess) return PS_ECUDA;
+    if (cudaEventRecord(ev_in[c], cp) != cudaSuccess) return PS_ECUDA;
   }
   pl->launches = 0;
   pl->nev = 0;
   Exec ex{pl, pl->ws, pl->dt, st, false};
   for (int c = 0; c < C; ++c) {
-    if (cudaStreamWaitEvent(st, pl->copy_ev[c + 1 < C ? c + 1 : C - 1], 0) != cudaSuccess) return PS_ECUDA;
-    if (pl->precision == PP_FP64) {
-      MomArgs<double> s1{(const double*)u, (const double*)v, (const double*)w, nullptr, nullptr, nullptr,
-                         (double*)ub, (double*)vb, (double*)wb, 0.0, 1.0, dt, nu, fx};
-      PP_TRY_N("momentum_1", launch_momentum<double>(g, ex.dt, s1, st, rows[c], rows[c + 1]));
-    } else {
-      MomArgs<float> s1{(const float*)u, (const float*)v, (const float*)w, nullptr, nullptr, nullptr,
-                        (float*)ub, (float*)vb, (float*)wb, 0.0, 1.0, dt, nu, fx};
-      PP_TRY_N("momentum_1", launch_momentum<float>(g, ex.dt, s1, st, rows[c], rows[c + 1]));
+    if (cudaStreamWaitEvent(st, ev_in[c + 1 < C ? c + 1 : C - 1], 0) != cudaSuccess) return PS_ECUDA;
+    MomArgs<T> s1{u, v, w, nullptr, nullptr, nullptr, ub, vb, wb, 0.0, 1.0, dt, nu, fx};
+    PP_TRY_N("momentum_1", launch_momentum<T>(g, ex.dt, s1, st, rows[c], rows[c + 1]));
+  }
+  MomArgs<T> s2{ub, vb, wb, u, v, w, u, v, w, 0.5, 0.5, 0.5 * dt, nu, fx};
+  PP_TRY_N("momentum_2", launch_momentum<T>(g, ex.dt, s2, st));
+  FwdArgs args = {};
+  args.u = u; args.v = v; args.w = w;
+  args.in_scale = 1.0 / dt;
+  T* p = p_dev ? p_dev : (T*)(pl->ws + pl->off_pbuf);
+  PP_RET((forward_and_core<T, T>(ex, FWD_DIV, args, GAUGE_ZERO)));
+  for (int c = 0; c < C; ++c) {
+    const size_t o = (size_t)rows[c] * plane;
+    PP_RET(inverse_x_rows<T>(ex, p, rows[c], rows[c + 1]));
+    if (p_h) {
+      if (cudaEventRecord(ev_p[c], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_p[c], 0) != cudaSuccess ||
+          cudaMemcpyAsync((T*)p_h + o, p + o, cells(c) * sizeof(T), cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+        return PS_ECUDA;
     }
+    PP_TRY_N("gradient", launch_gradient<T>(g, ex.dt, p, u, v, w, dt, st, rows[c], rows[c + 1]));
+    if (cudaEventRecord(ev_g[c], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_g[c], 0) != cudaSuccess)
+      return PS_ECUDA;
+    if (cudaMemcpyAsync((T*)u_h + o, u + o, cells(c) * sizeof(T), cudaMemcpyDeviceToHost, cp) != cudaSuccess ||
+        cudaMemcpyAsync((T*)w_h + o, w + o, cells(c) * sizeof(T), cudaMemcpyDeviceToHost, cp) != cudaSuccess ||
+        cudaMemcpyAsync((T*)v_h + o, v + o, faces(c) * sizeof(T), cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+      return PS_ECUDA;
   }
-  if (pl->precision == PP_FP64) {
-    MomArgs<double> s2{(const double*)ub, (const double*)vb, (const double*)wb, (const double*)u, (const double*)v,
-                       (const double*)w, (double*)u, (double*)v, (double*)w, 0.5, 0.5, 0.5 * dt, nu, fx};
-    PP_TRY_N("momentum_2", launch_momentum<double>(g, ex.dt, s2, st));
-  } else {
-    MomArgs<float> s2{(const float*)ub, (const float*)vb, (const float*)wb, (const float*)u, (const float*)v,
-                      (const float*)w, (float*)u, (float*)v, (float*)w, 0.5, 0.5, 0.5 * dt, nu, fx};
-    PP_TRY_N("momentum_2", launch_momentum<float>(g, ex.dt, s2, st));
-  }
-  return projection_impl(ex, u, v, w, p_out, dt);
+  if (cudaStreamSynchronize(cp) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return PS_ECUDA;
+  return PS_OK;
 }
 
 }  // namespace
@@ -928,14 +958,17 @@ poisson_status projection_timestep_host(poisson_plan_t pl, void* u_h, void* v_h,
   const bool overlap = pl->precision != PP_FP32_REFINED && !(pl->flags & (POISSON_CHECK_FINITE | POISSON_TIMING)) &&
                        pl->g.ny >= 2 * pp::HOST_CHUNKS;
   if (overlap) {
-    PP_RET(timestep_overlapped_input(pl, u_h, v_h, w_h, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx,
-                                     st));
-  } else {
-    if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-    if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-    if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
-    PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
+    if (pl->precision == PP_FP64)
+      return timestep_overlapped<double>(pl, u_h, v_h, w_h, p_h, (double*)u_d, (double*)v_d, (double*)w_d,
+                                         (double*)ub, (double*)vb, (double*)wb, p_h ? (double*)p_d : nullptr, dt, nu,
+                                         fx, st);
+    return timestep_overlapped<float>(pl, u_h, v_h, w_h, p_h, (float*)u_d, (float*)v_d, (float*)w_d, (float*)ub,
+                                      (float*)vb, (float*)wb, p_h ? (float*)p_d : nullptr, dt, nu, fx, st);
   }
+  if (cudaMemcpyAsync(u_d, u_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(v_d, v_h, nv, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  if (cudaMemcpyAsync(w_d, w_h, nc, cudaMemcpyHostToDevice, st) != cudaSuccess) return PS_ECUDA;
+  PP_RET(projection_timestep(pl, u_d, v_d, w_d, ub, vb, wb, p_h ? p_d : nullptr, dt, nu, fx, stream));
   if (cudaMemcpyAsync(u_h, u_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(v_h, v_d, nv, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;
   if (cudaMemcpyAsync(w_h, w_d, nc, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PS_ECUDA;

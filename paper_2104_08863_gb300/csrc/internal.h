@@ -179,7 +179,7 @@ cudaError_t launch_mode00(const Geometry& g, const DevTables& tb, GaugeMode gaug
 
 template <typename T>
 cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
-                            cudaStream_t st);
+                            cudaStream_t st, int jlo = 0, int jhi = -1);   // rows [jlo, jhi) (+ the top wall faces)
 
 template <typename T>
 cudaError_t launch_adjoint_epilogue(const Geometry& g, const DevTables& tb, const T* q, T* gu, T* gv, T* gw,
@@ -260,9 +260,10 @@ struct poisson_plan_s {
   int chain_streams = 1;
   cudaStream_t chain_st = nullptr;
   cudaEvent_t chain_ev[2] = {nullptr, nullptr};
-  // host-buffer timestep: the stream of its input copies and one event per row chunk (+ a start)
+  // host-buffer timestep: the stream of its copies and per row chunk the events of the input
+  // copies, the pressure and the corrected velocity (+ a start event)
   cudaStream_t copy_st = nullptr;
-  cudaEvent_t copy_ev[pp::HOST_CHUNKS + 1] = {};
+  cudaEvent_t copy_ev[3 * pp::HOST_CHUNKS + 1] = {};
   // POISSON_TIMING: one event pair around every launch of the last call
   std::vector<cudaEvent_t> ev;
   std::vector<const char*> ev_names;

@@ -14,14 +14,14 @@
 
 namespace pp {
 
+// Lines [lbeg, lend) of the (ny + 1) nz face lines (line = j nz + k).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gradient(Geometry g, const T* __restrict__ p, T* __restrict__ u,
                                                   T* __restrict__ v, T* __restrict__ w,
-                                                  const T* __restrict__ inv_h, T dt) {
+                                                  const T* __restrict__ inv_h, T dt, int lbeg, int lend) {
   const size_t plane = (size_t)g.nz * g.nx;
-  const int nlines = (g.ny + 1) * g.nz;
   const T cx = T(dt / g.dx), cz = T(dt / g.dz);
-  for (int line = blockIdx.x; line < nlines; line += gridDim.x)
+  for (int line = lbeg + blockIdx.x; line < lend; line += gridDim.x)
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
     const int j = line / g.nz, k = line - j * g.nz;
     const size_t idx = (size_t)line * g.nx + i;
@@ -144,8 +144,13 @@ template <> const float* inv_h_table<float>(const DevTables& tb) { return tb.f.i
 
 template <typename T>
 cudaError_t launch_gradient(const Geometry& g, const DevTables& tb, const T* p, T* u, T* v, T* w, double dt,
-                            cudaStream_t st) {
-  k_gradient<T><<<line_grid(g), line_block(g), 0, st>>>(g, p, u, v, w, inv_h_table<T>(tb), T(dt));
+                            cudaStream_t st, int jlo, int jhi) {
+  if (jhi < 0) jhi = g.ny;
+  if (jlo < 0 || jhi > g.ny || jhi <= jlo) return cudaErrorInvalidValue;
+  const int lbeg = jlo * g.nz, lend = (jhi == g.ny ? g.ny + 1 : jhi) * g.nz;
+  const int cap = line_grid(g);
+  k_gradient<T><<<lend - lbeg < cap ? lend - lbeg : cap, line_block(g), 0, st>>>(g, p, u, v, w, inv_h_table<T>(tb),
+                                                                                  T(dt), lbeg, lend);
   return cudaGetLastError();
 }
 
@@ -187,9 +192,9 @@ cudaError_t launch_check_finite(const T* x, size_t n, int* status, cudaStream_t 
 }
 
 template cudaError_t launch_gradient<double>(const Geometry&, const DevTables&, const double*, double*, double*,
-                                             double*, double, cudaStream_t);
+                                             double*, double, cudaStream_t, int, int);
 template cudaError_t launch_gradient<float>(const Geometry&, const DevTables&, const float*, float*, float*, float*,
-                                            double, cudaStream_t);
+                                            double, cudaStream_t, int, int);
 template cudaError_t launch_adjoint_epilogue<double>(const Geometry&, const DevTables&, const double*, double*,
                                                      double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_epilogue<float>(const Geometry&, const DevTables&, const float*, float*, float*,
