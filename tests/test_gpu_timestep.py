@@ -305,3 +305,25 @@ def test_host_timestep_equals_device_timestep(P, shape, prec):
     for got, want in zip(hosts, ref[:3]):
         assert float(np.max(np.abs(got.double().numpy() - want))) / scale <= tol
     assert relerr(ph.double().numpy(), ref[3]) <= (1e-3 if prec == "fp32" else 1e-10)
+
+
+def test_host_timestep_generic_fft_equals_device_timestep(P):
+    """The overlapped host timestep through the runtime-generic FFT kernels (POISSON_GENERIC_FFT),
+    whose inverse x-transform also runs on row chunks: bit for bit the device path."""
+    nx, ny, nz, s = 36, 40, 18, 1.6
+    case = W.ChannelCase("t", nx, ny, nz, s)
+    faces = W.tanh_faces(ny, s)
+    u, v, w = W.poiseuille_plus_noise(3, case)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP64, flags=P.POISSON_GENERIC_FFT, device=DEV)
+    ut, vt, wt = to_dev(u), to_dev(v), to_dev(w)
+    pt = torch.empty(ny, nz, nx, dtype=torch.float64, device=DEV)
+    scratch = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    hosts = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (u, v, w)]
+    ph = torch.empty(ny, nz, nx, dtype=torch.float64).pin_memory()
+    staging = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt), torch.empty_like(pt))
+    scratch_h = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt))
+    plan.timestep(ut, vt, wt, 1e-3, NU, FX, p_out=pt, scratch=scratch)
+    plan.timestep_host(*hosts, 1e-3, NU, FX, staging, scratch_h, p_h=ph)
+    torch.cuda.synchronize()
+    for dev_t, host_t in zip((ut, vt, wt, pt), (*hosts, ph)):
+        assert torch.equal(dev_t.cpu(), host_t)
