@@ -12,6 +12,7 @@
 //                     Poisson solve;
 //   k_gradient_pairs  u = u* - dt G p (Eq. 4) from the pairs and the solve's FP32 pressure pair,
 //                     FP64 out.
+#include "df2.cuh"
 #include "fpconv.cuh"
 #include "internal.h"
 
@@ -61,6 +62,46 @@ __device__ __forceinline__ df split(double x) {
   return r;
 }
 __device__ __forceinline__ float2 f2(df a) { return make_float2(a.hi, a.lo); }
+
+// The same operations on two values at once (df2.cuh): lane x one value, lane y the other, each
+// lane giving the scalar form's result.
+__device__ __forceinline__ df2 pk(df a, df b) { return df2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ df2 bc(df a) { return pk(a, a); }
+__device__ __forceinline__ df2 uadd2(df2 a, df2 b) {
+  const df2 s = two_sum2(a.hi, b.hi);
+  return df2{s.hi, f2add(s.lo, f2add(a.lo, b.lo))};
+}
+__device__ __forceinline__ df2 usub2(df2 a, df2 b) {
+  const df2 s = two_diff2(a.hi, b.hi);
+  return df2{s.hi, f2add(s.lo, f2sub(a.lo, b.lo))};
+}
+__device__ __forceinline__ df2 dmul2(df2 a, df2 b) {
+  const float2 p = f2mul(a.hi, b.hi);
+  float2 e = f2fma(a.hi, b.hi, make_float2(-p.x, -p.y));
+  e = f2fma(a.hi, b.lo, e);
+  e = f2fma(a.lo, b.hi, e);
+  return df2{p, e};
+}
+__device__ __forceinline__ df2 dtwice2(df2 a) {
+  return df2{f2mul(a.hi, make_float2(2.f, 2.f)), f2mul(a.lo, make_float2(2.f, 2.f))};
+}
+struct Acc2 { float2 S, C; };
+__device__ __forceinline__ void acc_prod2(Acc2& a, df2 c, df2 x) {
+  const float2 p = f2mul(c.hi, x.hi);
+  float2 e = f2fma(c.hi, x.hi, make_float2(-p.x, -p.y));
+  e = f2fma(c.hi, x.lo, e);
+  e = f2fma(c.lo, x.hi, e);
+  const df2 t = two_sum2(a.S, p);
+  a.S = t.hi;
+  a.C = f2add(a.C, f2add(t.lo, e));
+}
+// (S + C) normalised (quick TwoSum) lane by lane; lane x as the first pair, lane y the second.
+__device__ __forceinline__ void acc_out2(const Acc2& a, float2& x, float2& y) {
+  const float2 s = f2add(a.S, a.C);
+  const float2 lo = f2sub(a.C, f2sub(s, a.S));
+  x = make_float2(s.x, lo.x);
+  y = make_float2(s.y, lo.y);
+}
 
 constexpr int MTX = 32, MTZ = 8;
 
@@ -121,6 +162,7 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
   if (i >= nx || k >= nz) return;
   const df cDx = split(cdx), cDz = split(cdz);
   const df cAx = split(-0.25 * a.bdt / g.dx), cAz = split(-0.25 * a.bdt / g.dz);
+  const df2 cD_xz = pk(cDx, cDz), cD_zx = pk(cDz, cDx), cA_xz = pk(cAx, cAz), cA_zx = pk(cAz, cAx);
   const df fterm = split(a.bdt * a.fx);
   const df alpha = split(a.alpha);
   const bool has_base = a.bu != nullptr;
@@ -164,8 +206,12 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
     const df w_xm = ldp(sw + pc + oxm), w_xp = ldp(sw + pc + oxp), w_zm = ldp(sw + pc + ozm), w_zp = ldp(sw + pc + ozp);
     const df w_zp_xm = ldp(sw + pc + ozp_xm);
     const df v_xm = ldp(sv + pc + oxm), v_xp = ldp(sv + pc + oxp), v_zm = ldp(sv + pc + ozm), v_zp = ldp(sv + pc + ozp);
-    const df e_uv_n = top ? dmul(uadd(ldp(sv + pn + oxm), v_n), uadd(u_c, u_n)) : zero;
-    const df e_vw_n = top ? dmul(uadd(ldp(sv + pn + ozm), v_n), uadd(w_c, w_n)) : zero;
+    df e_uv_n = zero, e_vw_n = zero;   // fluxes through face j+1 (zero on the top wall), as a pair
+    if (top) {
+      const df2 e = dmul2(uadd2(pk(ldp(sv + pn + oxm), ldp(sv + pn + ozm)), bc(v_n)), uadd2(pk(u_c, w_c), pk(u_n, w_n)));
+      e_uv_n = df{e.hi.x, e.lo.x};
+      e_vw_n = df{e.hi.y, e.lo.y};
+    }
     const df e_uw = dmul(uadd(w_xm, w_c), uadd(u_zm, u_c));
     float2 bu2 = make_float2(0.f, 0.f), bw2 = bu2, bv2 = bu2;
     if (has_base) {   // the stage-2 base values, loaded together with the stencil
@@ -173,33 +219,25 @@ __global__ void __launch_bounds__(MTX * MTZ) k_momentum_df(Geometry g, MomArgsDF
       bw2 = a.bw[pc + oc];
       if (j >= 1) bv2 = a.bv[pc + oc];
     }
-    {   // u
-      Acc acc = acc_of(fterm);
-      if (has_base) acc_prod(acc, alpha, df{bu2.x, bu2.y});
-      acc_prod(acc, c.c0, u_c);
-      const df sx = uadd(u_xp, u_xm);
-      acc_prod(acc, cDx, sx);
-      acc_prod(acc, cAx, dmul(usub(u_xp, u_xm), uadd(sx, dtwice(u_c))));
-      acc_prod(acc, cDz, uadd(u_zp, u_zm));
-      acc_prod(acc, cAz, usub(dmul(uadd(w_zp_xm, w_zp), uadd(u_c, u_zp)), e_uw));
-      acc_prod(acc, c.cay, usub(e_uv_n, e_uv));
-      acc_prod(acc, c.ca, u_m);
-      acc_prod(acc, c.cc, u_n);
-      a.ou[pc + oc] = acc_out(acc);
-    }
-    {   // w
-      Acc acc{0.f, 0.f};
-      if (has_base) acc_prod(acc, alpha, df{bw2.x, bw2.y});
-      acc_prod(acc, c.c0, w_c);
-      const df sz = uadd(w_zp, w_zm);
-      acc_prod(acc, cDz, sz);
-      acc_prod(acc, cAz, dmul(usub(w_zp, w_zm), uadd(sz, dtwice(w_c))));
-      acc_prod(acc, cDx, uadd(w_xp, w_xm));
-      acc_prod(acc, cAx, usub(dmul(uadd(w_c, w_xp), uadd(u_zm_xp, u_xp)), e_uw));
-      acc_prod(acc, c.cay, usub(e_vw_n, e_vw));
-      acc_prod(acc, c.ca, w_m);
-      acc_prod(acc, c.cc, w_n);
-      a.ow[pc + oc] = acc_out(acc);
+    {   // u (lane x) and w (lane y): their equations mirror each other under x <-> z, term by term
+      Acc2 acc{make_float2(fterm.hi, 0.f), make_float2(fterm.lo, 0.f)};
+      if (has_base) acc_prod2(acc, bc(alpha), pk(df{bu2.x, bu2.y}, df{bw2.x, bw2.y}));
+      const df2 cuw = pk(u_c, w_c);
+      acc_prod2(acc, bc(c.c0), cuw);
+      const df2 xp = pk(u_xp, w_zp), xm = pk(u_xm, w_zm);   // along x for u, along z for w
+      const df2 s1 = uadd2(xp, xm);
+      acc_prod2(acc, cD_xz, s1);
+      acc_prod2(acc, cA_xz, dmul2(usub2(xp, xm), uadd2(s1, dtwice2(cuw))));
+      acc_prod2(acc, cD_zx, uadd2(pk(u_zp, w_xp), pk(u_zm, w_xm)));
+      acc_prod2(acc, cA_zx, usub2(dmul2(uadd2(pk(w_zp_xm, w_c), pk(w_zp, w_xp)), uadd2(pk(u_c, u_zm_xp), pk(u_zp, u_xp))),
+                                  bc(e_uw)));
+      acc_prod2(acc, bc(c.cay), usub2(pk(e_uv_n, e_vw_n), pk(e_uv, e_vw)));
+      acc_prod2(acc, bc(c.ca), pk(u_m, w_m));
+      acc_prod2(acc, bc(c.cc), pk(u_n, w_n));
+      float2 ou, ow;
+      acc_out2(acc, ou, ow);
+      a.ou[pc + oc] = ou;
+      a.ow[pc + oc] = ow;
     }
     if (j >= 1) {   // v at face j
       Acc acc{0.f, 0.f};

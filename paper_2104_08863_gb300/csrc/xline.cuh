@@ -4,6 +4,7 @@
 // its inverse, and compensated sums.
 #pragma once
 
+#include "df2.cuh"
 #include "fpconv.cuh"
 #include "internal.h"
 
@@ -267,31 +268,8 @@ __device__ __forceinline__ ResidLine resid_line(const Geometry& g, const FwdArgs
 
 __device__ __forceinline__ float2 ld_f2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// ---- the residual of a pair of cells in packed FP32x2 operations -----------------------------
-// Each FP32x2 instruction performs the same correctly rounded operation on both lanes (cell 0
-// in .x, cell 1 in .y), so the double-float algorithms below (TwoSum, TwoDiff, the FMA split of
-// a product, Dot2) run lane by lane at half the issued instructions.  The *_rn intrinsics are
-// never fused into FMAs by the compiler, which the error-free transformations rely on.
-struct df2 { float2 hi, lo; };
-
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b as one FMA with the multiplier -1 (exact product, one rounding: the correctly rounded
-// difference)
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// TwoSum / TwoDiff (Knuth) lane by lane: hi + lo == a +- b exactly.
-__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
-  const float2 s = f2add(a, b);
-  const float2 bp = f2sub(s, a);
-  return df2{s, f2add(f2sub(a, f2sub(s, bp)), f2sub(b, bp))};
-}
-__device__ __forceinline__ df2 two_diff2(float2 a, float2 b) {
-  const float2 s = f2sub(a, b);
-  const float2 bp = f2sub(s, a);
-  return df2{s, f2sub(f2sub(a, f2sub(s, bp)), f2add(b, bp))};
-}
+// ---- the residual of a pair of cells in packed FP32x2 operations (df2.cuh), cell 0 in .x and
+// cell 1 in .y
 __device__ __forceinline__ df2 diff_sum2(df2 a, df2 b) {
   const df2 s = two_sum2(a.hi, b.hi);
   return df2{s.hi, f2add(s.lo, f2add(a.lo, b.lo))};
