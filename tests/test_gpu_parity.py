@@ -400,3 +400,44 @@ def test_solve_adjoint_matches_oracle_transpose(P, prec, steps, tol):
     plan.solve_adjoint(same, out=same)   # in place
     torch.cuda.synchronize()
     assert relerr(same.double().cpu().numpy(), want) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "refined"])
+def test_host_projection_equals_device_projection(P, prec):
+    """projection_step_host (pinned host buffers in, results copied back) equals projection_step
+    on device buffers: bit for bit, except the refined form's pressure gauge (FP64 atomics)."""
+    nx, ny, nz = 48, 20, 24
+    faces = W.tanh_faces(ny, 1.7)
+    case = W.ChannelCase("h", nx, ny, nz, 1.7)
+    u, v, w = W.poiseuille_plus_noise(4, case)
+    precision = {"fp64": P.PP_FP64, "fp32": P.PP_FP32, "refined": P.PP_FP32_REFINED}[prec]
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    plan = P.Plan(nx, ny, nz, faces, precision=precision, refine_steps=2 if prec == "refined" else 1, device=DEV)
+    ut, vt, wt = (to_dev(a).to(dtype) for a in (u, v, w))
+    pt = torch.empty(ny, nz, nx, dtype=dtype, device=DEV)
+    plan.project(ut, vt, wt, 1e-3, p_out=pt)
+    hosts = [torch.from_numpy(np.ascontiguousarray(a)).to(dtype).pin_memory() for a in (u, v, w)]
+    ph = torch.empty(ny, nz, nx, dtype=dtype).pin_memory()
+    staging = (torch.empty_like(ut), torch.empty_like(vt), torch.empty_like(wt), torch.empty_like(pt))
+    plan.project_host(*hosts, 1e-3, staging, p_h=ph)
+    torch.cuda.synchronize()
+    for q, (dev_t, host_t) in enumerate(zip((ut, vt, wt, pt), (*hosts, ph))):
+        if prec == "refined":
+            d = float((dev_t.cpu() - host_t).abs().max() / host_t.abs().max())
+            assert d <= (1e-13 if q < 3 else 1e-10), (q, d)
+        else:
+            assert torch.equal(dev_t.cpu(), host_t)
+
+
+def test_fp64_fma_rate_is_measured_and_checks_its_scratch(P):
+    """poisson_fp64_fma_rate: a positive FP64 FMA throughput no larger than two FMAs per clock per
+    SM at the highest SM clock (the GB300 rate), and PS_EINVAL for a scratch buffer too small."""
+    import ctypes
+    from paper_2104_08863_gb300 import _native
+    rate = P.fp64_fma_rate(DEV)
+    props = torch.cuda.get_device_properties(DEV)
+    assert 0.0 < rate <= 2 * 2 * props.multi_processor_count * 2.2   # GFLOP/s, 2.2 GHz bound
+    small = torch.empty(64, dtype=torch.uint8, device=DEV)
+    out = ctypes.c_double()
+    st = _native.lib().poisson_fp64_fma_rate(small.data_ptr(), small.numel(), None, ctypes.byref(out))
+    assert st != 0
