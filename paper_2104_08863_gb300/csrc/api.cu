@@ -291,6 +291,8 @@ poisson_status poisson_plan_create(const poisson_desc* d, poisson_plan_t* out) {
   pl->off_pbuf = off;  off = align_up(off + rsz * (size_t)ny * g.nz * g.nx, 256);
   pl->off_pbuf2 = off;   // low FP32 part of the refined pressure
   if (d->precision == PP_FP32_REFINED) off = align_up(off + 4 * (size_t)ny * g.nz * g.nx, 256);
+  pl->off_r1 = off;      // the first correction's residual (FP32 pair per cell) for the later ones
+  if (pl->refine >= 2) off = align_up(off + 8 * (size_t)ny * g.nz * g.nx, 256);
   pl->off_scratch = off;
   if (L >= 0) off = align_up(off + 16 * (size_t)ny * (L + 1) * (2 * L + 1), 256);
   pl->off_tables = off; off = align_up(off + tab_bytes, 256);
@@ -532,9 +534,10 @@ poisson_status check_finite_uvw(Exec& ex, const void* u, const void* v, const vo
 // PP_FP32_REFINED keeps the pressure as an FP32 pair p = hi + lo in the workspace and never
 // issues per-point FP64 arithmetic (slow on GB300):
 //   hi = S32 f;  then for each of refine_steps corrections
-//   r = (f - <f>) - L_h (hi + lo) in double-float arithmetic;  d = S32 r;
+//   r = (f - <f>) - L_h (hi + lo) in double-float arithmetic (from the second correction on as
+//   r1 - L_h lo, r1 the first correction's residual kept as an FP32 pair);  d = S32 r;
 //   lo = d (first) or lo += d, and on the last correction p = hi + (lo + d) is written in FP64
-//   by exact integer assembly.
+//   (both FP32 terms widened exactly, one FP64 addition).
 // <f> is taken from the first solve's (0, 0) mode so that the FP32 transform of r carries no
 // large constant; the dy-weighted sum of p is accumulated by every inverse pass and each
 // correction's (0, 0) mode cancels it, so the gauge error of the FP32 transforms (invisible to
@@ -567,8 +570,14 @@ poisson_status solve_impl(Exec& ex, const void* rhs, void* p, bool pair_out = fa
     ra.in_scale = 1.0;
     split_f32(1.0 / (pl->g.dx * pl->g.dx), ra.idx2h, ra.idx2l);
     split_f32(1.0 / (pl->g.dz * pl->g.dz), ra.idz2h, ra.idz2l);
+    // The first correction forms r1 = (f - <f>) - L_h hi (and, when more follow, stores it as an
+    // FP32 pair); correction r then forms r1 - L_h lo, lo the sum of the corrections so far:
+    // the same f - <f> - L_h (hi + lo) by linearity, without re-reading f and hi.
+    float2* r1 = pl->refine >= 2 ? (float2*)(ex.ws + pl->off_r1) : nullptr;
     for (int r = 1; r <= pl->refine; ++r) {
-      ra.plo = r >= 2 ? lo : nullptr;
+      ra.p = r == 1 ? hi : lo;
+      ra.rin = r == 1 ? nullptr : r1;
+      ra.rout = r == 1 ? r1 : nullptr;
       PP_RET((forward_and_core<float, double>(ex, FWD_RESID, ra, GAUGE_OFFSET)));
       if (r < pl->refine) {
         PP_RET((inverse_x<float, float>(ex, r == 1 ? INV_STORE : INV_ACCUM, lo, true)));

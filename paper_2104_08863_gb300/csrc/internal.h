@@ -75,11 +75,15 @@ struct FwdArgs {
   const void* u;         // FWD_DIV / FWD_GRADT: face fields
   const void* v;
   const void* w;
-  const void* p;         // FWD_RESID: pressure, high FP32 part
-  const void* plo;       // FWD_RESID: pressure, low FP32 part (may be null)
+  const void* p;         // FWD_RESID: the FP32 pressure field the residual is formed of
   double in_scale;       // FWD_DIV: 1/dt; FWD_PLAIN: 1 (ignored for FP64 input to FP32)
   float idx2h, idx2l;    // FWD_RESID: 1/dx^2 and 1/dz^2 as double-floats
   float idz2h, idz2l;
+  // FWD_RESID, later corrections: r = rin - L_h p with rin a stored residual (one FP32 pair per
+  // cell) in place of (f - <f>); null for the first.  rout (may be null): the residual is also
+  // stored there as an FP32 pair.
+  const void* rin;
+  void* rout;
 };
 
 // Pointers of the FP32 pressure pair used by INV_FINAL.
@@ -248,7 +252,8 @@ struct poisson_plan_s {
   std::vector<double> faces, dy, h, a, c, lamx, lamz;
   std::vector<unsigned char> host_tables;   // staging image of the device tables
   // workspace layout (byte offsets)
-  size_t off_spec, off_pbuf, off_pbuf2, off_scratch, off_tables, off_status, off_acc, off_tri, off_red, ws_bytes;
+  size_t off_spec, off_pbuf, off_pbuf2, off_r1, off_scratch, off_tables, off_status, off_acc, off_tri, off_red,
+      ws_bytes;
   bool has_tri;   // per-mode PDD factor tables in the workspace (FP64 plans; FP32 plans with m = ny/P outside the register kernel's set)
   size_t tab_offsets[32];
   unsigned char* ws;

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(XTile<T, M>::THREADS, XTile<T, M>::MINB)
         const ResidLine R = resid_line(g, args, tt, tb, line, mh, ml);
 #pragma unroll
         for (int n = threadIdx.x; n < M; n += THREADS) {
-          const float2 r = resid_pair_line2(R, n);
+          const float2 r = R.rin ? resid_pair_line2<true>(R, n) : resid_pair_line2<false>(R, n);
           buf[padi<T>(t * M + n)] = mk<T>(r.x, r.y);
         }
       } else {
@@ -391,7 +391,7 @@ cudaError_t launch_fwd_x_stockham(const Geometry& g, const DevTables& tb, const 
     // refinement residual: warp-per-line residual into shared memory, then the register transform
     if (mode == FWD_RESID) {
       using R = XReg<M>;
-      auto k = k_fwd_x_reg_resid<M>;
+      auto k = args.rin ? k_fwd_x_reg_resid<M, true> : k_fwd_x_reg_resid<M, false>;
       if ((e = set_smem(k, R::SMEM)) != cudaSuccess) return e;
       k<<<(nlines + R::LPB - 1) / R::LPB, R::THREADS, R::SMEM, st>>>(g, args, tt, tb, spec, nlines);
       return cudaGetLastError();

@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(XReg<M>::THREADS, 3)
   fwd_x_reg_tile<TI, M, MODE>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
 }
 
-// Refinement residual r = (f - <f>) - L_h p (FP64 rhs f, FP32-pair pressure; resid_pair_line2)
-// transformed into the FP32 half spectrum.  Phase 0: one warp per line forms the residual pairs
-// in natural order in shared memory (the line's set-up amortised over M/32 pairs per lane, loads
-// coalesced across the warp); the register transform then reads its inputs from there (one more
+// Refinement residual r = (f - <f>) - L_h p, or rin - L_h p for a later correction
+// (resid_pair_line2), transformed into the FP32 half spectrum.  Phase 0: one warp per line forms
+// the residual pairs in natural order in shared memory (the line's set-up amortised over M/32
+// pairs per lane, loads coalesced across the warp); the register transform then reads its inputs from there (one more
 // barrier, since pass 1 overwrites the natural order with the transposed rows of the same line).
-template <int M>
+template <int M, bool RIN>
 __device__ __forceinline__ void fwd_x_reg_resid_tile(const Geometry& g, const FwdArgs& args, const Tables<float>& tt,
                                                      const DevTables& tb, cplx<float>* __restrict__ spec,
                                                      int nlines, int tile, unsigned char* smem_raw) {
@@ -136,7 +136,7 @@ __device__ __forceinline__ void fwd_x_reg_resid_tile(const Geometry& g, const Fw
         const ResidLine R = resid_line(g, args, tt, tb, line, mh, ml);
 #pragma unroll 3
         for (int n = lane; n < M; n += 32) {
-          const float2 r = resid_pair_line2(R, n);
+          const float2 r = resid_pair_line2<RIN>(R, n);
           nat[n] = mk<float>(r.x, r.y);
         }
       } else {
@@ -199,12 +199,13 @@ __device__ __forceinline__ void fwd_x_reg_resid_tile(const Geometry& g, const Fw
   }
 }
 
-template <int M>
+// RIN: a later correction (the stored first residual in place of f - <f>, see resid_line).
+template <int M, bool RIN>
 __global__ void __launch_bounds__(XReg<M>::THREADS, 3)
     k_fwd_x_reg_resid(Geometry g, FwdArgs args, Tables<float> tt, DevTables tb, cplx<float>* __restrict__ spec,
                       int nlines) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fwd_x_reg_resid_tile<M>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
+  fwd_x_reg_resid_tile<M, RIN>(g, args, tt, tb, spec, nlines, blockIdx.x, smem_raw);
 }
 
 // Inverse x-transform of the FP32 half spectrum into an FP32 field with the epilogue MODE

@@ -66,14 +66,16 @@ __device__ __forceinline__ void gradT_pair(const Geometry& g, const TI* __restri
 }
 
 // Refinement residual r = (f - <f>) - L_h p at cells (j,k,i0) and (j,k,i0+1), where f is the
-// FP64 right-hand side and p = hi + lo the pressure carried as an FP32 pair.  Removing <f>
-// keeps the FP32 transform of r free of a large constant whose rounding noise would otherwise
-// leak into the weakly damped low modes at every step.  L_h p is formed in double-float
-// arithmetic on FP32 units: neighbour differences of hi are exact (TwoDiff) and those of lo are
-// added in double-float (near the walls the stencil terms of lo cancel strongly, so plain FP32
-// would floor the refinement), products with the double-float stencil coefficients recover
-// their rounding error with FMAs, and the sums carry a compensation term, so r is accurate to
-// ~2^-47 of the stencil terms.
+// FP64 right-hand side and p the first solve's FP32 pressure hi; with a stored residual rin of
+// the same solve (the first correction's, an FP32 pair per cell) a later correction forms
+// r = rin - L_h lo instead, lo the FP32 sum of the corrections so far (by linearity the same
+// f - <f> - L_h (hi + lo)).  Removing <f> keeps the FP32 transform of r free of a large constant
+// whose rounding noise would otherwise leak into the weakly damped low modes at every step.
+// L_h p is formed in double-float arithmetic on FP32 units: neighbour differences of the FP32
+// field are exact (TwoDiff; near the walls the stencil terms cancel strongly, so plain FP32
+// differences would floor the refinement), products with the double-float stencil coefficients
+// recover their rounding error with FMAs, and the sums carry a compensation term, so r is
+// accurate to ~2^-47 of the stencil terms.
 template <typename TT>
 __device__ __forceinline__ void residual_pair_df(const Geometry& g, const FwdArgs& args, const TT& tt,
                                                  const DevTables& tb, int j, int k, int i0, float& r0, float& r1) {
@@ -89,14 +91,11 @@ __device__ __forceinline__ void residual_pair_df(const Geometry& g, const FwdArg
   float mh, ml;
   f64_split(tb.acc[0], mh, ml);
   const float* P = reinterpret_cast<const float*>(args.p);
-  const float* Q = reinterpret_cast<const float*>(args.plo);
   const double* f = reinterpret_cast<const double*>(args.in);
-  // neighbour difference d(n) = p_n - p_c of p = hi + lo, exact in hi and carried in double-float
-  auto diff = [&](size_t n, size_t o) -> df {
-    df d = two_diff_df(P[n], P[o]);
-    if (Q) d = df_add(d, two_diff_df(Q[n], Q[o]));
-    return d;
-  };
+  const float2* rin = reinterpret_cast<const float2*>(args.rin);
+  float2* rout = reinterpret_cast<float2*>(args.rout);
+  // neighbour difference d(n) = p_n - p_c, exact as a double-float
+  auto diff = [&](size_t n, size_t o) -> df { return two_diff_df(P[n], P[o]); };
   float out[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -106,10 +105,17 @@ __device__ __forceinline__ void residual_pair_df(const Geometry& g, const FwdArg
     L = df_add(L, df_mul(df_add(diff(rkp + i0 + c, o), diff(rkm + i0 + c, o)), cz));
     if (has_lo) L = df_add(L, df_mul(diff(o - plane, o), ca));
     if (has_hi) L = df_add(L, df_mul(diff(o + plane, o), cc));
-    float fh, fl;
-    f64_split(f[o], fh, fl);
-    df r = df_add(df{fh, fl}, df{-mh, -ml});
+    df r;
+    if (rin) {
+      const float2 q = rin[o];
+      r = df{q.x, q.y};
+    } else {
+      float fh, fl;
+      f64_split(f[o], fh, fl);
+      r = df_add(df{fh, fl}, df{-mh, -ml});
+    }
     r = df_add(r, df_neg(L));
+    if (rout) rout[o] = make_float2(r.hi, r.lo);
     out[c] = r.hi + r.lo;
   }
   r0 = out[0];
@@ -228,9 +234,10 @@ __device__ __forceinline__ void final_store(double* o, float2 h, float2 l, float
 // exactly into p + pi by an FMA, the p are summed with TwoSum and all error terms go into one
 // correction, giving the result as if computed with twice the FP32 precision.
 struct ResidLine {
-  const float* P;      // pressure hi of this line
-  const float* Q;      // pressure lo of this line (null when absent)
+  const float* P;      // the FP32 pressure field (hi, or lo for a later correction) of this line
   const double* f;     // rhs of this line
+  const float2* rin;   // stored residual of this line (replaces f - <f>; null when absent)
+  float2* rout;        // the residual stored as an FP32 pair (null: not stored)
   int ozm, ozp;        // element offsets of the z-1 and z+1 lines (periodic)
   int oym, oyp;        // offsets of the y-1 and y+1 lines (0 at a wall: no such face)
   bool hym, hyp;       // the y-1 / y+1 face exists
@@ -248,8 +255,9 @@ __device__ __forceinline__ ResidLine resid_line(const Geometry& g, const FwdArgs
   const size_t row = (size_t)line * g.nx;
   ResidLine R;
   R.P = reinterpret_cast<const float*>(args.p) + row;
-  R.Q = args.plo ? reinterpret_cast<const float*>(args.plo) + row : nullptr;
   R.f = reinterpret_cast<const double*>(args.in) + row;
+  R.rin = args.rin ? reinterpret_cast<const float2*>(args.rin) + row : nullptr;
+  R.rout = args.rout ? reinterpret_cast<float2*>(args.rout) + row : nullptr;
   R.ozm = (k == 0 ? g.nz - 1 : -1) * g.nx;
   R.ozp = (k + 1 == g.nz ? 1 - g.nz : 1) * g.nx;
   R.hym = j >= 1;
@@ -290,8 +298,10 @@ __device__ __forceinline__ void dot2_sub2(float2& S, float2& C, float2 ch, float
 struct ResidIn {
   float2 pc, zm, zp, ym, yp;
   float pm, pp;
-  double2 fv;
+  double2 fv;   // rhs (the first correction)
+  float4 rv;    // stored residual pairs of the two cells (later corrections)
 };
+template <bool RIN>
 __device__ __forceinline__ ResidIn resid_load(const ResidLine& R, int n) {
   const int i0 = 2 * n;
   const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
@@ -304,54 +314,53 @@ __device__ __forceinline__ ResidIn resid_load(const ResidLine& R, int n) {
   in.zp = ld_f2(R.P + (i0 + R.ozp));
   in.ym = R.hym ? ld_f2(R.P + (i0 + R.oym)) : make_float2(0.f, 0.f);
   in.yp = R.hyp ? ld_f2(R.P + (i0 + R.oyp)) : make_float2(0.f, 0.f);
-  in.fv = *reinterpret_cast<const double2*>(R.f + i0);
+  if constexpr (RIN) {
+    in.rv = *reinterpret_cast<const float4*>(R.rin + i0);
+  } else {
+    in.fv = *reinterpret_cast<const double2*>(R.f + i0);
+  }
   return in;
 }
 
+template <bool RIN>
 __device__ __forceinline__ float2 resid_pair_from(const ResidLine& R, int n, const ResidIn& in) {
   const int i0 = 2 * n;
-  const int im = i0 == 0 ? R.nx - 1 : i0 - 1;
-  const int ip = i0 + 2 == R.nx ? 0 : i0 + 2;
   const float2 pc = in.pc, zm = in.zm, zp = in.zp, ym = in.ym, yp = in.yp;
   const float pm = in.pm, pp = in.pp;
-  const double2 fv = in.fv;
   // x-neighbours: cell 0 pairs (p_{i-1}, p_{i+1} = cell 1), cell 1 pairs (p_{i+2}, p_i = cell 0);
   // the difference between the two cells is shared with opposite signs
   df2 dout = two_diff2(make_float2(pm, pp), pc);
   const df2 d01 = two_diff2(make_float2(pc.y, pc.x), pc);   // (p1 - p0, p0 - p1), exact
   df2 dz0 = two_diff2(zp, pc), dz1 = two_diff2(zm, pc);
   df2 dy0 = two_diff2(ym, pc), dy1 = two_diff2(yp, pc);
-  if (R.Q) {
-    const float2 qc = ld_f2(R.Q + i0);
-    const float qm = R.Q[im], qp = R.Q[ip];
-    const float2 qzm = ld_f2(R.Q + (i0 + R.ozm)), qzp = ld_f2(R.Q + (i0 + R.ozp));
-    const float2 qym = R.hym ? ld_f2(R.Q + (i0 + R.oym)) : make_float2(0.f, 0.f);
-    const float2 qyp = R.hyp ? ld_f2(R.Q + (i0 + R.oyp)) : make_float2(0.f, 0.f);
-    dout = diff_sum2(dout, two_diff2(make_float2(qm, qp), qc));
-    const df2 q01 = two_diff2(make_float2(qc.y, qc.x), qc);
-    const df2 e01 = diff_sum2(d01, q01);
-    dz0 = diff_sum2(dz0, two_diff2(qzp, qc));
-    dz1 = diff_sum2(dz1, two_diff2(qzm, qc));
-    if (R.hym) dy0 = diff_sum2(dy0, two_diff2(qym, qc));
-    if (R.hyp) dy1 = diff_sum2(dy1, two_diff2(qyp, qc));
-    dout = diff_sum2(dout, e01);
+  dout = diff_sum2(dout, d01);
+  float2 S, C;
+  if constexpr (RIN) {   // the stored residual (already without <f>)
+    S = make_float2(in.rv.x, in.rv.z);
+    C = make_float2(in.rv.y, in.rv.w);
   } else {
-    dout = diff_sum2(dout, d01);
+    float2 fh, fl;
+    f64_split(in.fv.x, fh.x, fl.x);
+    f64_split(in.fv.y, fh.y, fl.y);
+    const df2 s0 = two_sum2(fh, make_float2(-R.mh, -R.mh));
+    S = s0.hi;
+    C = f2add(s0.lo, f2sub(fl, make_float2(R.ml, R.ml)));
   }
-  float2 fh, fl;
-  f64_split(fv.x, fh.x, fl.x);
-  f64_split(fv.y, fh.y, fl.y);
-  const df2 s0 = two_sum2(fh, make_float2(-R.mh, -R.mh));
-  float2 S = s0.hi, C = f2add(s0.lo, f2sub(fl, make_float2(R.ml, R.ml)));
   dot2_sub2(S, C, make_float2(R.cx.hi, R.cx.hi), make_float2(R.cx.lo, R.cx.lo), dout);
   dot2_sub2(S, C, make_float2(R.cz.hi, R.cz.hi), make_float2(R.cz.lo, R.cz.lo), diff_sum2(dz0, dz1));
   if (R.hym) dot2_sub2(S, C, make_float2(R.ca.hi, R.ca.hi), make_float2(R.ca.lo, R.ca.lo), dy0);
   if (R.hyp) dot2_sub2(S, C, make_float2(R.cc.hi, R.cc.hi), make_float2(R.cc.lo, R.cc.lo), dy1);
-  return f2add(S, C);
+  const float2 r = f2add(S, C);
+  if (R.rout) {   // the residual as normalised pairs (quick TwoSum of S and C), one per cell
+    const float2 e = f2sub(C, f2sub(r, S));
+    *reinterpret_cast<float4*>(R.rout + i0) = make_float4(r.x, e.x, r.y, e.y);
+  }
+  return r;
 }
 
+template <bool RIN>
 __device__ __forceinline__ float2 resid_pair_line2(const ResidLine& R, int n) {
-  return resid_pair_from(R, n, resid_load(R, n));
+  return resid_pair_from<RIN>(R, n, resid_load<RIN>(R, n));
 }
 
 }  // namespace pp

@@ -359,6 +359,23 @@ def test_fp32_refined_solve_register_residual_lengths(P, nx, ny, nz, steps):
     assert plan.device_status() == 0
 
 
+@pytest.mark.parametrize("steps", [2, 3])
+def test_fp32_refined_solve_generic_fft(P, steps):
+    """The refined solve through the runtime-generic kernels (POISSON_GENERIC_FFT; Nx/2 = 18 has
+    no specialised transform either): their residual producer forms the first correction's
+    residual from f and stores it, and the later ones from that stored residual."""
+    nx, ny, nz = 36, 12, 18
+    faces = W.tanh_faces(ny, 2.0)
+    g = oracle.Grid(nx, nz, faces)
+    f = oracle.divergence(g, *W.random_velocity(8, nx, ny, nz))
+    want = oracle.solve(g, f)
+    plan = P.Plan(nx, ny, nz, faces, precision=P.PP_FP32_REFINED, pdd_parts=1, fp64_low_modes=4,
+                  refine_steps=steps, flags=P.POISSON_GENERIC_FFT, device=DEV)
+    got = plan.solve(to_dev(f))
+    torch.cuda.synchronize()
+    assert relerr(got.cpu().numpy(), want) <= 1e-12
+
+
 def test_bounded_wait_runs_out_and_reports_timeout(P):
     """POISSON_SELFTEST_WAIT makes the bulk-copy-staged x-transform skip its first copy: its
     bounded mbarrier wait gives up (~2 s), the device status reads PS_ETIMEOUT, and the context
