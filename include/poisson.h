@@ -100,7 +100,9 @@ typedef struct {
  * of Eq. 9 and the FFT twiddles.  *out receives an opaque handle owned by the library. */
 poisson_status poisson_plan_create(const poisson_desc* desc, poisson_plan_t* out);
 
-/* Bytes of device workspace the plan needs (spectral buffer, tables, status word). */
+/* Bytes of device workspace the plan needs (spectral buffer, tables, status word; for
+ * PP_FP32_REFINED the FP32 pressure pair, and with refine_steps >= 2 the first correction's
+ * residual as an FP32 pair per cell, 8 bytes per point). */
 poisson_status poisson_workspace_size(poisson_plan_t plan, size_t* bytes);
 
 /* Attach caller-owned device workspace (>= poisson_workspace_size bytes, 256-byte aligned)
