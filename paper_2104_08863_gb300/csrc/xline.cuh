@@ -169,7 +169,7 @@ __device__ __forceinline__ cplx<T> fwd_load(const Geometry& g, const FwdArgs& ar
                    reinterpret_cast<const TI*>(args.w), j, k, i0, TI(1.0 / g.dx), TI(1.0 / g.dz),
                    TI(tt.inv_h[j]), TI(tt.inv_h[j + 1]), TI(tt.inv_dy[j]), f0, f1);
     return mk<T>(T(f0), T(f1));
-  } else {  // FWD_RESID: FP64 rhs, FP32-pair pressure, double-float arithmetic
+  } else {  // FWD_RESID: FP64 rhs (or a stored residual), FP32 pressure field, double-float arithmetic
     if constexpr (sizeof(T) == 4) {
       float r0, r1;
       residual_pair_df(g, args, tt, tb, j, k, i0, r0, r1);
@@ -199,7 +199,7 @@ __device__ __forceinline__ cplx<T> inv_pre(int kx, cplx<T> Xk, cplx<T> Xm, cplx<
 }
 
 // Epilogue of the inverse x-transform: store, accumulate, or (INV_FINAL) assemble the FP64
-// pressure hi + (lo + v) of the refined solve by integer arithmetic (faithful to one FP64 ulp).
+// pressure hi + (lo + v) of the refined solve (exact widenings, one FP64 addition).
 template <typename T, typename TO, int MODE>
 __device__ __forceinline__ void inv_store(TO* o, size_t off, T x0, T x1, const PairArgs& pair) {
   if constexpr (MODE == INV_ACCUM) {
